@@ -1,0 +1,18 @@
+"""FP64 CPU oracle for the nonsmooth sphere DEM step of arXiv 2501.05300.
+
+TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only users; the library never imports this package.
+It shares no code with the CUDA library.
+
+Parity status per function (what pins it is in tests/test_oracle_*.py):
+  detection (sphere-sphere)   pinned: KD-tree pair query (scipy), brute force
+  detection (sphere-geometry) pinned: dense surface sampling of the primitive
+  normal law + SPOOK          pinned: Hertz head-on collision closed form,
+                              static resting column, energy / momentum laws
+  Coulomb friction            pinned: sphere on an inclined plane (stick/slip)
+  rolling resistance          pinned: rolling sphere on an incline
+  Jacobi sweep                pinned: converges to the MCP solution found by an
+                              independent projected Gauss-Seidel on tiny cases
+  step-size / iteration rules pinned: Table 3 of the paper
+"""
+from .binding import Oracle, OracleParams, Geom, detect, load, lib_path, build  # noqa: F401

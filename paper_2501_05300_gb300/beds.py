@@ -1,0 +1,240 @@
+"""Seeded synthetic inputs: particle beds and the rigid geometry around them.
+
+Only input construction lives here (positions, radii, walls, plates); none of
+the contact law, solver or integrator.  Beds follow the paper's recipe
+(Sec. 3.1): layers of particles whose diameter is uniform in [0.9, 1.1] of the
+layer's nominal size, coarser layers below finer ones (Sec. 2.1).  Instead of
+emitting and relaxing particles, each layer starts as a jittered cubic lattice
+that a few hundred settling steps compact to a random dense packing.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+PLANE, BOX, CYLINDER = 0, 1, 2
+IDENT = (1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0)
+
+# dry-sand material of the paper (Sec. 3.1); density and friction as overridden
+# by the workloads below where they state their own values
+RHO_PAPER, E_PAPER, NU_PAPER, MU_T_PAPER, MU_R_PAPER = 2200.0, 1e9, 0.15, 0.3, 0.02
+
+
+@dataclass
+class GeomSpec:
+    """A rigid, kinematic primitive.  R is row-major; column k is local axis k.
+    plane: c a point on it, normal = local z (solid below);
+    box: c centre, he half extents; cylinder: c centre, axis local z,
+    he[0] radius, he[2] half height."""
+    type: int
+    c: tuple
+    R: tuple = IDENT
+    he: tuple = (0.0, 0.0, 0.0)
+    v: tuple = (0.0, 0.0, 0.0)
+    w: tuple = (0.0, 0.0, 0.0)
+    E: float = E_PAPER
+    nu: float = NU_PAPER
+    mu_t: float = 0.5
+    mu_r: float = 0.02
+
+
+@dataclass
+class Material:
+    rho: float = 2600.0
+    E: float = E_PAPER
+    nu: float = NU_PAPER
+    mu_t: float = 0.5
+    mu_r: float = 0.02
+
+
+@dataclass
+class Bed:
+    """Particles (x float64 [N,3], r float32 [N], ids 0..N-1) plus geometry."""
+    x: np.ndarray
+    r: np.ndarray
+    geoms: list = field(default_factory=list)
+    material: Material = field(default_factory=Material)
+    name: str = ""
+    plate: int = -1                  # index of the driven plate primitive, -1 none
+    plate_parts: tuple = ()          # primitives moved together with the plate
+    box: tuple = (0.0, 0.0, 0.0)     # container extents
+
+    @property
+    def n(self) -> int:
+        return int(self.r.shape[0])
+
+    def v(self):
+        return np.zeros((self.n, 3), np.float32)
+
+
+def plane(point, normal, mu_t=0.0, mu_r=0.0):
+    """Plane through `point` whose outward normal is `normal` (solid behind it)."""
+    nz = np.asarray(normal, float)
+    nz = nz / np.linalg.norm(nz)
+    a = np.array([1.0, 0, 0]) if abs(nz[0]) < 0.9 else np.array([0, 1.0, 0])
+    nx = a - (a @ nz) * nz
+    nx /= np.linalg.norm(nx)
+    ny = np.cross(nz, nx)
+    Rm = np.stack([nx, ny, nz], axis=1)
+    return GeomSpec(PLANE, tuple(map(float, point)), tuple(Rm.reshape(-1)), mu_t=mu_t, mu_r=mu_r)
+
+
+def open_box_walls(lx, ly, mu_wall=0.0):
+    """Floor z=0 and four side walls of [0,lx]x[0,ly]; frictionless walls as in
+    the paper's containers (Sec. 3.1 and 3.3)."""
+    return [plane((0, 0, 0), (0, 0, 1), mu_wall, mu_wall),
+            plane((0, 0, 0), (1, 0, 0), mu_wall, mu_wall),
+            plane((lx, 0, 0), (-1, 0, 0), mu_wall, mu_wall),
+            plane((0, 0, 0), (0, 1, 0), mu_wall, mu_wall),
+            plane((0, ly, 0), (0, -1, 0), mu_wall, mu_wall)]
+
+
+def _uniform_radii(rng, r_nom, n, spread):
+    return (r_nom * rng.uniform(1.0 - spread, 1.0 + spread, n)).astype(np.float32)
+
+
+def lattice_layer(rng, lx, ly, z0, n_target, r_nom, spread=0.1, gap=0.03, margin=None):
+    """n_target spheres of radius r_nom*U[1-spread,1+spread] on a jittered cubic
+    lattice inside [0,lx]x[0,ly], sub-layers stacked upwards from z0.  The
+    lattice spacing leaves a gap so that no two spheres overlap.  Returns
+    (x, r, z_top)."""
+    rmax = r_nom * (1 + spread)
+    s = 2 * rmax * (1 + gap)
+    jit = 0.45 * (s - 2 * rmax)
+    margin = rmax * 1.001 + jit if margin is None else margin
+    nx = max(1, int(math.floor((lx - 2 * margin) / s)) + 1)
+    ny = max(1, int(math.floor((ly - 2 * margin) / s)) + 1)
+    per = nx * ny
+    nz = int(math.ceil(n_target / per))
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+    order = np.lexsort((ix, iy, iz))[:n_target]
+    ix, iy, iz = ix[order], iy[order], iz[order]
+    x = np.stack([margin + ix * s, margin + iy * s, z0 + margin + iz * s], axis=1)
+    x += rng.uniform(-jit, jit, x.shape)
+    r = _uniform_radii(rng, r_nom, len(x), spread)
+    return x.astype(np.float64), r, z0 + nz * s
+
+
+def layered_bed(lx, ly, layers_bottom_up, spread=0.1, phi=0.636, seed=0, gap=0.03):
+    """Layers (r_nominal, settled_thickness) from the bottom up.  Each layer
+    holds round(lx ly thickness phi / <V>) spheres, <V> the mean sphere volume
+    of its radius distribution; the lattice is looser than phi and settles."""
+    rng = np.random.default_rng(seed)
+    xs, rs, z = [], [], 0.0
+    for r_nom, thick in layers_bottom_up:
+        # <r^3> of r_nom*U[1-s,1+s] is r_nom^3 ((1+s)^4-(1-s)^4)/(8s)
+        m3 = r_nom ** 3 * (((1 + spread) ** 4 - (1 - spread) ** 4) / (8 * spread) if spread > 0 else 1.0)
+        vmean = 4.0 / 3.0 * math.pi * m3
+        n_target = int(round(lx * ly * thick * phi / vmean))
+        if n_target == 0:
+            continue
+        x, r, z = lattice_layer(rng, lx, ly, z, n_target, r_nom, spread, gap)
+        xs.append(x)
+        rs.append(r)
+    return np.concatenate(xs), np.concatenate(rs)
+
+
+# --------------------------------------------------------------------------- #
+# the workloads                                                               #
+# --------------------------------------------------------------------------- #
+def settling_box(n=2000, seed=2502):
+    """2,000 spheres, r ~ U[5,6] mm, in a 0.1 x 0.1 x 0.3 m box on a jittered
+    lattice (spacing 12.5 mm); settles under gravity (rho 2600, mu 0.5)."""
+    rng = np.random.default_rng(seed)
+    s, lx = 12.5e-3, 0.1
+    per_side = int(math.floor((lx - 12e-3) / s)) + 1
+    per = per_side * per_side
+    idx = np.arange(n)
+    ix, iy, iz = idx % per_side, (idx // per_side) % per_side, idx // per
+    x = np.stack([6.22e-3 + ix * s, 6.22e-3 + iy * s, 6.22e-3 + iz * s], axis=1).astype(np.float64)
+    x += rng.uniform(-0.2e-3, 0.2e-3, x.shape)
+    r = rng.uniform(5e-3, 6e-3, n).astype(np.float32)
+    mat = Material(rho=2600.0, mu_t=0.5, mu_r=0.02)
+    return Bed(x, r, open_box_walls(lx, lx), mat, name=f"settling box, {n} spheres r~U[5,6] mm",
+               box=(lx, lx, 0.3))
+
+
+def refined_layers(top_r=2.5e-3, top_thickness=0.02, growth=2.0, n_coarser=3, depth=0.25):
+    """Layer list (bottom up) of a refined bed: top layer r = top_r, thickness
+    top_thickness = eta d_0; each layer below doubles r and its thickness
+    (d_n = r d_{n-1}, thickness eta d_n, Sec. 2.1); the coarsest fills the rest."""
+    eta = top_thickness / (2 * top_r)
+    tops = []
+    r, z = top_r, 0.0
+    for i in range(n_coarser + 1):
+        t = eta * 2 * r
+        if i == n_coarser:
+            t = depth - z
+        tops.append((r, t))
+        z += t
+        r *= growth
+    return list(reversed(tops))
+
+
+def refined_sinkage_bed(lx=0.89, ly=0.89, depth=0.25, seed=2503, phi=0.636):
+    """Refined bed for plate sinkage: r = 2.5 mm in the top 2 cm, doubling per
+    layer below (5, 10, 20 mm; max size ratio 8), 10% radius spread.  A
+    0.89 x 0.89 m footprint gives about 200k spheres (the 0.4 x 0.4 m bin of
+    the same layering holds about 41k).  A rigid disc plate (0.1 m diameter)
+    above the centre is the driven geometry."""
+    layers = refined_layers(depth=depth)
+    x, r = layered_bed(lx, ly, layers, spread=0.1, phi=phi, seed=seed)
+    geoms = open_box_walls(lx, ly)
+    zs = float((x[:, 2] + r).max())
+    plate = GeomSpec(CYLINDER, (lx / 2, ly / 2, zs + 0.01 + 0.005), he=(0.05, 0.0, 0.005),
+                     mu_t=0.5, mu_r=0.02)
+    geoms.append(plate)
+    mat = Material(rho=2600.0, mu_t=0.5, mu_r=0.02)
+    return Bed(x, r, geoms, mat, name=f"refined bed {lx}x{ly}x{depth} m, r 2.5/5/10/20 mm",
+               plate=len(geoms) - 1, plate_parts=(len(geoms) - 1,), box=(lx, ly, depth))
+
+
+def fine_shear_bed(lx=1.0, ly=0.5, depth=0.25, seed=2504, phi=0.636, r_nom=2.5e-3):
+    """Homogeneous fine bed (r = 2.5 mm, 10% spread) with a 0.3 x 0.3 m plate
+    carrying three transverse grousers 43 mm deep and 25.5 mm long at the
+    bottom (Sec. 3.3); the plate and grousers are separate boxes."""
+    x, r = layered_bed(lx, ly, [(r_nom, depth)], spread=0.1, phi=phi, seed=seed)
+    geoms = open_box_walls(lx, ly)
+    zs = float((x[:, 2] + r).max())
+    cx, cy = 0.25 * lx, ly / 2
+    t_plate = 0.01
+    z_plate = zs + 0.043 + 0.002 + t_plate / 2
+    parts = [GeomSpec(BOX, (cx, cy, z_plate), he=(0.15, 0.15, t_plate / 2), mu_t=0.5, mu_r=0.02)]
+    for gx in (-0.1, 0.0, 0.1):
+        parts.append(GeomSpec(BOX, (cx + gx, cy, z_plate - t_plate / 2 - 0.0215),
+                              he=(0.01275, 0.15, 0.0215), mu_t=0.5, mu_r=0.02))
+    first = len(geoms)
+    geoms.extend(parts)
+    mat = Material(rho=2600.0, mu_t=0.5, mu_r=0.02)
+    return Bed(x, r, geoms, mat, name=f"fine bed {lx}x{ly}x{depth} m, r 2.5 mm",
+               plate=first, plate_parts=tuple(range(first, len(geoms))), box=(lx, ly, depth))
+
+
+def random_cloud(n, seed, rmin=2e-3, rmax=6e-3, box=0.05, overlap_ok=False, vscale=0.0):
+    """Spheres placed uniformly at random in [-box, box]^3 (overlaps allowed
+    unless overlap_ok is False, then rejection sampled); velocities uniform in
+    [-vscale, vscale]."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(rmin, rmax, n).astype(np.float32)
+    if overlap_ok:
+        x = rng.uniform(-box, box, (n, 3))
+    else:
+        x = np.zeros((n, 3))
+        for i in range(n):
+            for _ in range(10000):
+                c = rng.uniform(-box, box, 3)
+                if i == 0 or (np.linalg.norm(x[:i] - c, axis=1) > r[:i].astype(float) + float(r[i])).all():
+                    break
+            x[i] = c
+    v = rng.uniform(-vscale, vscale, (n, 3)).astype(np.float32)
+    w = rng.uniform(-vscale, vscale, (n, 3)).astype(np.float32) * 100.0
+    return x.astype(np.float64), r, v, w
+
+
+def column(n, r=5e-3):
+    """n equal spheres stacked on the floor plane, just touching."""
+    x = np.array([[0.0, 0.0, r + 2 * r * k] for k in range(n)])
+    return x, np.full(n, r, np.float32)

@@ -1,0 +1,111 @@
+"""Pins of the host-side rules (Eqs. 1, 8-10) against the paper's tables and
+identities, and of the seeded bed generator."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+from paper_2501_05300_gb300 import beds, rules
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def table3():
+    rows = [l.split() for l in open(os.path.join(GOLD, "table3_uniform_beds.txt"))
+            if l.strip() and not l.startswith("#")]
+    return np.array(rows, dtype=float)
+
+
+def test_timestep_rule_reproduces_table3():
+    """Eq. 9 with rho = 2200 kg/m^3, sigma = 50 kPa and one tolerance eps gives
+    Table 3's time steps within 10% (the table rounds to 2 digits)."""
+    t = table3()
+    d, dt = t[:, 0] * 1e-3, t[:, 3] * 1e-3
+    # the simplified form dt = d sqrt(eps rho / (6 sigma)) of Sec. 2.2
+    for eps in (0.0189,):
+        pred = np.array([rules.timestep(di, eps, 2200.0, 50e3) for di in d])
+        simple = d * np.sqrt(eps * 2200.0 / (6 * 50e3))
+        assert np.allclose(pred, simple, rtol=1e-12)
+        assert np.all(np.abs(pred / dt - 1) < 0.10), pred / dt
+
+
+def test_iteration_rule_slope_matches_table3():
+    """Eq. 8 with n_d = h/d (h = 600 mm) is linear in n_d with slope 0.1/eps;
+    Table 3's N_it rise by that slope with eps = 0.02, up to a constant offset
+    the paper does not state.  The table's N_it are multiples of 25, which over
+    the n_d span of 50 leaves the fitted slope uncertain by about 7%."""
+    t = table3()
+    nd = 0.6 / (t[:, 0] * 1e-3)
+    slope = np.polyfit(nd, t[:, 2], 1)[0]
+    assert abs(slope / (0.1 / 0.02) - 1) < 0.08
+    assert rules.n_iterations(50.0, 0.02) == 250
+    assert rules.n_iterations(14.75, 0.02) == 74
+
+
+def test_layer_identities():
+    """z_n = eta d0 (r^{n+1}-1)/(r-1) and d_n = d0/r + (r-1)/(r eta) z_n (Sec. 2.1)."""
+    for d0, r, eta in [(8.5e-3, 1.5, 2.0), (5e-3, 2.0, 4.0), (8.5e-3, 1.25, 10.0)]:
+        zb = rules.layer_bottoms(d0, r, eta, 8)
+        for n, z in enumerate(zb):
+            assert abs(z - eta * d0 * (r ** (n + 1) - 1) / (r - 1)) < 1e-12
+            dn = d0 / r + (r - 1) / (r * eta) * z
+            assert abs(dn - d0 * r ** n) < 1e-12
+        gam = rules.discrete_aggressiveness(r, eta)
+        # the discrete profile is the continuous one with d_min = d0/r offset
+        assert abs(rules.refinement_profile(zb[3], d0 / r, gam, 1.0) - d0 * r ** 3) < 1e-12
+
+
+def test_refinement_profile_eq1():
+    d = [rules.refinement_profile(z, 8.5e-3, 0.05, 30e-3) for z in (0.0, 0.1, 0.43, 0.5)]
+    assert d[0] == pytest.approx(8.5e-3)
+    assert d[1] == pytest.approx(8.5e-3 + 0.005)
+    assert d[2] == pytest.approx(30e-3)          # z_max = 0.43
+    assert d[3] == pytest.approx(30e-3)
+    assert rules.z_max(8.5e-3, 0.05, 30e-3) == pytest.approx(0.43)
+
+
+def test_network_length_eq10():
+    # the refined sinkage bed: eta 4, d 5 -> 40 mm, r 2, z_max 0.14, h 0.25
+    nd = rules.network_length_refined(4.0, 5e-3, 40e-3, 2.0, 0.25, 0.14)
+    assert nd == pytest.approx(12 + 2.75)
+    # a uniform bed has no refined layers: n_d = h / d
+    assert rules.network_length_refined(4.0, 8.5e-3, 8.5e-3, 2.0, 0.6, 0.0) == pytest.approx(0.6 / 8.5e-3)
+
+
+def test_refined_layers_follow_sec21():
+    layers = beds.refined_layers()
+    rs = [l[0] for l in layers][::-1]
+    th = [l[1] for l in layers][::-1]
+    assert rs == pytest.approx([2.5e-3, 5e-3, 10e-3, 20e-3])
+    assert th[:3] == pytest.approx([0.02, 0.04, 0.08])     # thickness eta d_n, eta = 4
+    assert sum(th) == pytest.approx(0.25)
+
+
+@pytest.mark.parametrize("maker", [lambda: beds.refined_sinkage_bed(0.3, 0.3),
+                                   lambda: beds.settling_box()])
+def test_generated_beds_have_no_overlaps_and_paper_spread(maker):
+    b = maker()
+    x, r = b.x, b.r.astype(np.float64)
+    tree = cKDTree(x)
+    pairs = tree.query_pairs(2 * r.max(), output_type="ndarray")
+    if len(pairs):
+        d = np.linalg.norm(x[pairs[:, 0]] - x[pairs[:, 1]], axis=1)
+        assert (d > r[pairs[:, 0]] + r[pairs[:, 1]]).all()
+    # every sphere is inside the container
+    assert (x[:, 0] - r >= 0).all() and (x[:, 1] - r >= 0).all() and (x[:, 2] - r >= 0).all()
+    assert (x[:, 0] + r <= b.box[0]).all() and (x[:, 1] + r <= b.box[1]).all()
+
+
+def test_refined_bed_radius_bands():
+    b = beds.refined_sinkage_bed(0.3, 0.3)
+    for rn in (2.5e-3, 5e-3, 10e-3, 20e-3):
+        m = (b.r > 0.85 * rn) & (b.r < 1.15 * rn)
+        assert m.sum() > 0
+        assert b.r[m].min() >= 0.9 * rn * (1 - 1e-6) and b.r[m].max() <= 1.1 * rn * (1 + 1e-6)
+
+
+def test_refined_bed_count_is_about_200k():
+    b = beds.refined_sinkage_bed()
+    assert 190_000 < b.n < 215_000

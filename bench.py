@@ -1,0 +1,320 @@
+"""Benchmark: particle-steps/s of the refined-bed pressure-sinkage workload.
+
+Workload: about 200k spheres in layers of r = 2.5 / 5 / 10 / 20 mm (10% spread,
+top 2 cm fine, radius doubling per layer below, size ratio 8) on a
+0.89 x 0.89 x 0.25 m bed; a rigid 0.1 m diameter disc plate pushed down at
+0.01 m/s; dt = 1e-5 s; N_it = 74 Jacobi sweeps (Eq. 8 with n_d from Eq. 10).
+A step is one full SPOOK time step of the whole bed: cell lists, contact
+detection, contact rows and warm start, 74 sweeps, integration and the plate
+force reduction.  Inputs are seeded and synthetic; the bed is first settled
+(untimed) from a jittered lattice.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload (the oracle is the reference here).
+Multi-GPU runs (torchrun) advance one independent replica bed per rank: the
+single bed is not sharded.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2501_05300_gb300 import beds, rules  # noqa: E402
+
+METRIC = "particle-steps/s"
+DT = 1e-5
+PLATE_V = 0.01
+# refined bed: eta = 4, d 5 -> 40 mm, growth 2, z_max = 0.14 m, h = 0.25 m
+N_IT = rules.n_iterations(rules.network_length_refined(4.0, 5e-3, 40e-3, 2.0, 0.25, 0.14), 0.02)
+# algorithmic bytes of one Jacobi sweep (per contact: 48 B row data + 24 B
+# impulse read + 24 B written; per particle: v,w read, v*,w* read, v,w written)
+BYTES_PER_CONTACT = 96
+BYTES_PER_BODY = 96
+# one step's host traffic in the end-to-end mode: plate velocity in (6 doubles),
+# plate force/torque accumulators (6 int64), fault flag and plate pose out
+H2D_PER_STEP = 6 * 8
+D2H_PER_STEP = 6 * 8 + 4 + 192
+WORKLOAD = ("refined bed pressure-sinkage: ~200k spheres, r 2.5/5/10/20 mm +-10%, "
+            "0.89x0.89x0.25 m, 0.1 m disc plate at 0.01 m/s, dt 1e-5 s, N_it 74")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [q.strip() for q in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax = max(smax, float(p[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def settle_and_place(torch, dem, spec, settle_steps):
+    """Settle the lattice (generation friction mu_t 0.1, mu_r 0.01, Sec. 3.1)
+    at dt = 2e-4 (Eq. 9 allows ~2.7e-4 for d = 5 mm under the bed's own
+    weight), then put the plate 0.5 mm above the surface under it."""
+    plate = spec.plate
+    geoms = [g for g in spec.geoms]
+    hold = beds.GeomSpec(**{**spec.geoms[plate].__dict__})
+    hold.c = (hold.c[0], hold.c[1], hold.c[2] + 1.0)          # out of the way while settling
+    geoms[plate] = hold
+    b = dem.Bed(spec.x, spec.r, geoms=geoms, rho=spec.material.rho, mu_t=0.1, mu_r=0.01,
+                n_it=N_IT, dt=2e-4)
+    b.step(settle_steps)
+    x, v, w = b.read_state()
+    b.close()
+    pc = spec.geoms[plate]
+    under = (x[:, 0] - pc.c[0]) ** 2 + (x[:, 1] - pc.c[1]) ** 2 <= pc.he[0] ** 2
+    top = float((x[under, 2] + spec.r[under]).max()) if under.any() else float((x[:, 2] + spec.r).max())
+    placed = beds.GeomSpec(**{**pc.__dict__})
+    placed.c = (pc.c[0], pc.c[1], top + 0.0005 + pc.he[2])
+    geoms = list(spec.geoms)
+    geoms[plate] = placed
+    return x, v, w, geoms
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2501_05300_gb300 import dem
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.cuda.current_device()
+    spec = beds.refined_sinkage_bed()
+    x, v, w, geoms = settle_and_place(torch, dem, spec, args.settle)
+    m = spec.material
+    bed = dem.Bed(x, spec.r, v=v, w=w, geoms=geoms, rho=m.rho, mu_t=m.mu_t, mu_r=m.mu_r,
+                  n_it=N_IT, dt=DT)
+    pl = spec.plate
+    # approach: bring the plate into contact (untimed), then 0.01 m/s
+    bed.apply_plate_velocity(pl, (0.0, 0.0, -0.05))
+    bed.step(200)
+    bed.apply_plate_velocity(pl, (0.0, 0.0, -PLATE_V))
+    bed.step(args.warmup)
+    bed.sync()
+    info = bed.info()
+    n = info.n
+    settled = (info.contacts + info.geom_contacts) / max(n, 1)
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    bed.set_timing(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        torch.cuda.nvtx.range_push("dem_timed")
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            bed.step(1)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms, jac_ms, tsteps = bed.read_timing()
+    bed.set_timing(False)
+    info = bed.info()
+    contacts = info.contacts + info.geom_contacts
+    f, t, sink = bed.read_forces(pl)
+    ms_per_step = step_ms / max(tsteps, 1)
+    if world > 1:
+        tt = torch.tensor([ms_per_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_per_step = float(tt.item())
+    value = world * n / (ms_per_step * 1e-3)
+    # dominant kernel: one Jacobi sweep
+    sweep_ms = jac_ms / max(tsteps * N_IT, 1)
+    alg_bytes = BYTES_PER_CONTACT * contacts + BYTES_PER_BODY * n
+    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    resorts = sum(1 for s in range(info.steps - args.steps, info.steps) if s % 20 == 0)
+    launches = args.steps * info.kernels_per_step + resorts * info.kernels_per_resort
+
+    # end to end through the C ABI with host buffers: plate command in, force out
+    e2e_steps = max(10, min(args.steps, 200))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        bed.apply_plate_velocity(pl, (0.0, 0.0, -PLATE_V))
+        bed.step(1)
+        bed.read_forces(pl)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * n * e2e_steps / e2e_s
+    bed.close()
+    return dict(value=value, ms_per_step=ms_per_step, n=n, contacts=contacts, sweep_ms=sweep_ms,
+                alg_bytes=alg_bytes, achieved=achieved, peak=peak, launches=launches,
+                clocks=clk.summary(), e2e=e2e_value, force=f.tolist(), sinkage=sink, wall=wall,
+                settled=settled)
+
+
+def squeezed_bed(lx, ly, squeeze=0.84):
+    """The layered bed generator's lattice, every coordinate pulled towards the
+    bed's centre by `squeeze`, so that neighbours overlap (about 2.6 contacts
+    per particle) without any settling run."""
+    spec = beds.refined_sinkage_bed(lx=lx, ly=ly)
+    c = spec.x.mean(0)
+    x = c + (spec.x - c) * squeeze
+    return spec, x
+
+
+def oracle_sample(lx=0.89, ly=0.89, max_steps=1, seconds_budget=30.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload:
+    the same layered bed, squeezed to contact, stepped with N_it = 74 until
+    max_steps or the time budget is reached."""
+    import oracle
+    spec, x = squeezed_bed(lx, ly)
+    m = spec.material
+    geoms = [oracle.Geom(g.type, g.c, g.R, g.he, g.v, g.w, g.E, g.nu, g.mu_t, g.mu_r) for g in spec.geoms]
+    p = oracle.OracleParams(rho=m.rho, mu_t=m.mu_t, mu_r=m.mu_r, dt=DT, n_it=N_IT)
+    o = oracle.Oracle(p, x, spec.r.astype(np.float64), geoms=geoms)
+    n = spec.n
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget or steps >= max_steps:
+            break
+    cores = oracle.load().orc_threads()
+    return dict(value=n * steps / el, n=n, steps=steps, seconds=el, cores=cores,
+                contacts=len(o.contacts()[0]), footprint=(lx, ly))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--settle", type=int, default=2000)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        s = oracle_sample(0.3, 0.3, max_steps=args.steps, seconds_budget=120.0)
+        sample = (f"FP64 oracle, {s['steps']} steps of a {s['n']}-sphere 0.3x0.3 m cut of the same "
+                  f"layered bed squeezed to contact ({s['contacts']} contacts), N_it {N_IT}")
+        line = {"metric": METRIC, "value": s["value"], "unit": METRIC, "n_gpus": args.gpus,
+                "steps": s["steps"], "warmup": 0, "ms_per_step": 1e3 * s["seconds"] / s["steps"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD, "particles": s["n"], "sample": sample},
+                "cpu_baseline": {"value": s["value"], "unit": METRIC, "cores": s["cores"],
+                                 "kind": "oracle", "sample": sample},
+                "e2e": {"value": s["value"], "unit": METRIC, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = run_gpu(args, rank, world)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": r["n"], "contacts": r["contacts"],
+                   "n_it": N_IT, "dt": DT, "parallelism": f"replicas{world}",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "contacts_per_particle_at_start": r["settled"]},
+        "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
+                     "frac": r["achieved"] / r["peak"], "traffic": None,
+                     "kernel": "k_jacobi (one projected Jacobi sweep)",
+                     "sweep_us": 1e3 * r["sweep_ms"], "alg_bytes_per_sweep": r["alg_bytes"],
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+        "e2e": {"value": r["e2e"], "unit": METRIC, "h2d_bytes_per_step": H2D_PER_STEP,
+                "d2h_bytes_per_step": D2H_PER_STEP},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "contact_updates_per_s": r["contacts"] * N_IT / (r["ms_per_step"] * 1e-3),
+        "plate": {"force_N": r["force"], "sinkage_m": r["sinkage"]},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        s = oracle_sample()
+        line["cpu_baseline"] = {"value": s["value"], "unit": METRIC, "cores": s["cores"], "kind": "oracle",
+                                "sample": (f"{s['steps']} FP64 oracle step(s) of the full {s['n']}-sphere "
+                                           f"bed squeezed to contact ({s['contacts']} contacts), "
+                                           f"N_it {N_IT}, {s['seconds']:.1f} s")}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

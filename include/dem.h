@@ -1,0 +1,176 @@
+/*
+ * dem.h -- C ABI of the GB300 (sm_103a) nonsmooth sphere DEM library.
+ *
+ * The library advances beds of spheres with the time-implicit ("nonsmooth")
+ * DEM of arXiv 2501.05300, Sec. 2.2: Newton-Euler bodies with contact
+ * constraints (Eq. 2), a Hertz-mapped compliant normal constraint
+ * (g_n = delta^{e_H}, eps_n = e_H/k_n, k_n = E* sqrt(d*)/3), Coulomb friction
+ * and rolling resistance (Eqs. 5-7), time-integrated with the SPOOK stepper
+ * and solved with a fixed number N_it (Eq. 8) of projected Jacobi sweeps,
+ * warm-started from the previous step.  Beds may be locally refined: particle
+ * size grows with depth (Sec. 2.1), so the broad phase keeps one cell grid per
+ * radius band.
+ *
+ * Conventions for every call:
+ *  - SI units.  Positions are double, velocities and material data float.
+ *  - Array arguments are caller-owned.  Inputs are copied; they may live in
+ *    host memory or in device memory of the bed's GPU (unified addressing).
+ *  - Every call returns a dem_status and never throws.  dem_last_error()
+ *    returns a thread-local message describing the last failure.
+ *  - dem_step only enqueues work on the bed's CUDA stream and returns.  Faults
+ *    found on the device (contact capacity exceeded, non-finite state) are
+ *    latched in a device flag; the next synchronising call (dem_read_*,
+ *    dem_sync) returns them, and the bed then refuses to step (DEM_ERR_STATE)
+ *    until it is destroyed.
+ *  - Particles are identified by their index in the arrays given to
+ *    dem_create_bed ("stable id").  The library reorders particles internally
+ *    (Morton order) but every read returns stable-id order.
+ */
+#ifndef DEM_H
+#define DEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dem_status {
+    DEM_OK = 0,
+    DEM_ERR_ARG = 1,        /* invalid argument; nothing was changed */
+    DEM_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    DEM_ERR_CAPACITY = 3,   /* contact storage overflowed during a step */
+    DEM_ERR_TIMEOUT = 4,    /* a bounded device wait gave up */
+    DEM_ERR_NONFINITE = 5,  /* a non-finite velocity appeared */
+    DEM_ERR_STATE = 6       /* the bed holds a latched device fault */
+} dem_status;
+
+typedef enum dem_geom_type {
+    DEM_GEOM_PLANE = 0,     /* c: point on the plane; normal = local z; solid behind */
+    DEM_GEOM_BOX = 1,       /* c: centre; he: half extents (oriented box) */
+    DEM_GEOM_CYLINDER = 2   /* c: centre; axis local z; he[0] radius, he[2] half height */
+} dem_geom_type;
+
+/* A rigid kinematic primitive: bin walls, plates, grousers (Sec. 3.3).  Its
+ * velocity is prescribed (a velocity motor, Sec. 2.2: G_j v = u_j(t)). */
+typedef struct dem_geom {
+    int32_t type;           /* dem_geom_type */
+    double c[3];            /* reference point / centre [m] */
+    double R[9];            /* row-major rotation; column k = local axis k in world */
+    double he[3];           /* box half extents; cylinder (radius, unused, half height) [m] */
+    double v[3];            /* velocity of c [m/s] */
+    double w[3];            /* angular velocity about c [rad/s] */
+    float E, nu;            /* Young's modulus [Pa] and Poisson ratio of the geometry */
+    float mu_t, mu_r;       /* sphere-geometry friction and rolling resistance (Eqs. 6-7) */
+} dem_geom;
+
+/* Optional device allocator; when NULL the library uses cudaMallocAsync on the
+ * bed's stream.  `stream` is the bed's cudaStream_t. */
+typedef void* (*dem_alloc_fn)(size_t bytes, void* ctx, void* stream);
+typedef void (*dem_free_fn)(void* ptr, void* ctx, void* stream);
+
+typedef struct dem_bed_desc {
+    int32_t n;                  /* particles, >= 0 */
+    const double* pos;          /* [3n] centres (x,y,z) [m], required if n > 0 */
+    const float* radius;        /* [n] radii [m] > 0, required if n > 0 */
+    const float* vel;           /* [3n] initial velocities [m/s], NULL = 0 */
+    const float* omega;         /* [3n] initial angular velocities [rad/s], NULL = 0 */
+    const float* inv_mass;      /* [n] override of 1/m, NULL = solid spheres of density rho */
+    const float* inv_inertia;   /* [n] override of 1/I, NULL = 1/(2/5 m r^2) */
+    float rho;                  /* particle density [kg/m^3] (Sec. 3.1) */
+    float E, nu;                /* particle Young's modulus [Pa], Poisson ratio (Sec. 3.1) */
+    float mu_t, mu_r;           /* particle-particle friction / rolling resistance (Eqs. 6-7) */
+    float e_H;                  /* gap exponent: 1.25 Hertz, 1.0 linear (Sec. 2.2) */
+    float damp_steps;           /* damping time tau in steps, tau/dt (Sec. 2.2: 4.5) */
+    float dt;                   /* time step [s] (Eq. 9) */
+    int32_t n_it;               /* Jacobi sweeps per step (Eq. 8), >= 0 */
+    float gravity[3];           /* [m/s^2] */
+    float kn_scale;             /* factor on k_n; 1 = the paper's k_n */
+    float eps_reg;              /* tangential/rolling compliance, relative to the normal one */
+    float delta_floor;          /* overlap floor in the Hertz Jacobian [m]; 0 = 1e-6 * d_min */
+    int32_t n_geom;             /* number of primitives, >= 0 */
+    const dem_geom* geom;       /* [n_geom], host memory */
+    int64_t contact_capacity;   /* sphere-sphere contacts; 0 = 8 n (grows never) */
+    int32_t resort_every;       /* Morton re-sort period in steps; 0 = 20 */
+    float level_ratio;          /* radius ratio per grid level; 0 = 2 */
+    dem_alloc_fn alloc;         /* optional allocator (see above) */
+    dem_free_fn free_fn;
+    void* alloc_ctx;
+} dem_bed_desc;
+
+typedef struct dem_bed dem_bed;   /* opaque, library-owned */
+
+typedef struct dem_info {
+    int32_t n;                  /* particles */
+    int32_t n_levels;           /* broad-phase grid levels */
+    int64_t n_cells;            /* total cells over all levels */
+    int64_t contacts;           /* sphere-sphere contacts of the last step */
+    int64_t geom_contacts;      /* sphere-geometry contacts of the last step */
+    int64_t steps;              /* steps taken */
+    int64_t contact_capacity;
+    int32_t kernels_per_step;   /* kernel launches of one plain (non-resort) step */
+    int32_t kernels_per_resort; /* extra launches of a re-sort */
+} dem_info;
+
+/* Create a bed from particles, materials and geometry.
+ * stream: a cudaStream_t (NULL = the library creates a non-blocking stream).
+ * Synchronous: returns when the bed is ready.  On failure *out is NULL. */
+dem_status dem_create_bed(const dem_bed_desc* desc, void* stream, dem_bed** out);
+
+/* Enqueue nsteps time steps (detection, SPOOK rows, N_it Jacobi sweeps,
+ * integration; Sec. 2.2) on the bed's stream.  Asynchronous. */
+dem_status dem_step(dem_bed* bed, int32_t nsteps);
+
+/* Prescribe the velocity of primitive `geom_id` from the next step on
+ * (motor constraint, Sec. 2.2).  v [m/s], w [rad/s] host arrays of 3. */
+dem_status dem_apply_plate_velocity(dem_bed* bed, int32_t geom_id, const double v[3],
+                                    const double w[3]);
+
+/* Contact force f [N] and torque t [N m] about the primitive's centre exerted
+ * by the particles during the last step (impulse / dt), and the sinkage [m]:
+ * the height of the particle surface under the primitive at creation minus the
+ * current lowest point of the primitive (Sec. 3.3).  Synchronises the stream.
+ * Any of f, t, sinkage may be NULL. */
+dem_status dem_read_forces(dem_bed* bed, int32_t geom_id, double f[3], double t[3],
+                           double* sinkage);
+
+/* Copy the state in stable-id order: pos [3n] double, vel [3n], omega [3n]
+ * float; any may be NULL.  cap = capacity in particles (>= n).  Synchronises. */
+dem_status dem_read_state(dem_bed* bed, double* pos, float* vel, float* omega, int32_t cap);
+
+/* Copy the contacts of the last step, in no particular order.  For contact k:
+ * key_a[k] = stable id of body a; key_b[k] = stable id of body b, or -(g+1)
+ * for primitive g; lam7[7k..7k+6] = impulse on a in world frame
+ * (p_n, p_t.x, p_t.y, p_t.z, p_r.x, p_r.y, p_r.z) with the normal pointing from
+ * b to a; delta[k] = overlap [m].  Any output may be NULL.  Writes at most cap
+ * contacts and returns the total in *count.  Synchronises. */
+dem_status dem_read_contacts(dem_bed* bed, int64_t cap, int32_t* key_a, int32_t* key_b,
+                             float* lam7, float* delta, int64_t* count);
+
+/* Current pose and velocity of primitive geom_id.  Synchronises. */
+dem_status dem_read_geom(dem_bed* bed, int32_t geom_id, dem_geom* out);
+
+/* Wait for the bed's stream; returns a latched device fault if any. */
+dem_status dem_sync(dem_bed* bed);
+
+/* Sizes and counters (synchronises). */
+dem_status dem_get_info(dem_bed* bed, dem_info* out);
+
+/* Record CUDA events around the Jacobi sweeps of every step (enable != 0).
+ * dem_read_timing returns, for the steps enqueued since timing was enabled,
+ * the summed milliseconds of the whole steps and of their Jacobi sweeps and
+ * the number of steps.  Synchronises. */
+dem_status dem_set_timing(dem_bed* bed, int32_t enable);
+dem_status dem_read_timing(dem_bed* bed, double* step_ms, double* jacobi_ms, int64_t* steps);
+
+/* Release all device memory of the bed.  NULL is accepted. */
+dem_status dem_destroy_bed(dem_bed* bed);
+
+/* Thread-local description of the last error ("" if none). */
+const char* dem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEM_H */

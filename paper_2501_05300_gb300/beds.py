@@ -4,8 +4,9 @@ Only input construction lives here (positions, radii, walls, plates); none of
 the contact law, solver or integrator.  Beds follow the paper's recipe
 (Sec. 3.1): layers of particles whose diameter is uniform in [0.9, 1.1] of the
 layer's nominal size, coarser layers below finer ones (Sec. 2.1).  Instead of
-emitting and relaxing particles, each layer starts as a jittered cubic lattice
-that a few hundred settling steps compact to a random dense packing.
+emitting and relaxing particles, each layer starts as a jittered face-centred
+cubic lattice with a small gap between neighbours, which settling under
+gravity compacts to a dense packing.
 """
 from __future__ import annotations
 
@@ -96,32 +97,41 @@ def _uniform_radii(rng, r_nom, n, spread):
 
 
 def lattice_layer(rng, lx, ly, z0, n_target, r_nom, spread=0.1, gap=0.03, margin=None):
-    """n_target spheres of radius r_nom*U[1-spread,1+spread] on a jittered cubic
-    lattice inside [0,lx]x[0,ly], sub-layers stacked upwards from z0.  The
-    lattice spacing leaves a gap so that no two spheres overlap.  Returns
-    (x, r, z_top)."""
+    """n_target spheres of radius r_nom*U[1-spread,1+spread] on a jittered
+    face-centred cubic lattice (triangular layers stacked ABC) inside
+    [0,lx]x[0,ly], layers stacked upwards from z0.  The nearest-neighbour
+    distance leaves a gap so that no two spheres overlap.  Returns (x, r, z_top)."""
     rmax = r_nom * (1 + spread)
-    s = 2 * rmax * (1 + gap)
-    jit = 0.45 * (s - 2 * rmax)
+    a = 2 * rmax * (1 + gap)                 # nearest-neighbour distance
+    jit = 0.45 * (a - 2 * rmax)
     margin = rmax * 1.001 + jit if margin is None else margin
-    nx = max(1, int(math.floor((lx - 2 * margin) / s)) + 1)
-    ny = max(1, int(math.floor((ly - 2 * margin) / s)) + 1)
-    per = nx * ny
-    nz = int(math.ceil(n_target / per))
-    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
-    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
-    order = np.lexsort((ix, iy, iz))[:n_target]
-    ix, iy, iz = ix[order], iy[order], iz[order]
-    x = np.stack([margin + ix * s, margin + iy * s, z0 + margin + iz * s], axis=1)
-    x += rng.uniform(-jit, jit, x.shape)
+    dy, dz = a * math.sqrt(3.0) / 2.0, a * math.sqrt(2.0 / 3.0)
+    pts, k = [], 0
+    count = 0
+    while count < n_target:
+        sx, sy = (k % 3) * a / 2.0, (k % 3) * a * math.sqrt(3.0) / 6.0
+        ys = np.arange(margin + sy, ly - margin + 1e-12, dy)
+        rows = []
+        for j, y in enumerate(ys):
+            xs = np.arange(margin + sx + (a / 2.0 if j % 2 else 0.0), lx - margin + 1e-12, a)
+            rows.append(np.stack([xs, np.full_like(xs, y), np.full_like(xs, z0 + margin + k * dz)], 1))
+        layer = np.concatenate(rows) if rows else np.zeros((0, 3))
+        pts.append(layer)
+        count += len(layer)
+        k += 1
+        if k > 100000:
+            raise ValueError("footprint too small for one sphere")
+    x = np.concatenate(pts)[:n_target]
+    x = x + rng.uniform(-jit, jit, x.shape)
     r = _uniform_radii(rng, r_nom, len(x), spread)
-    return x.astype(np.float64), r, z0 + nz * s
+    return x.astype(np.float64), r, z0 + margin + (k - 1) * dz + rmax * 1.001 + jit
 
 
 def layered_bed(lx, ly, layers_bottom_up, spread=0.1, phi=0.636, seed=0, gap=0.03):
     """Layers (r_nominal, settled_thickness) from the bottom up.  Each layer
     holds round(lx ly thickness phi / <V>) spheres, <V> the mean sphere volume
-    of its radius distribution; the lattice is looser than phi and settles."""
+    of its radius distribution; the lattice is a little looser than phi and
+    settles."""
     rng = np.random.default_rng(seed)
     xs, rs, z = [], [], 0.0
     for r_nom, thick in layers_bottom_up:

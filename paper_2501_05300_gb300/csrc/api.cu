@@ -1,0 +1,790 @@
+// C ABI of the DEM library (include/dem.h): bed creation, the per-step graph
+// of kernels, read-back and error reporting.
+//
+// One step (Sec. 2.2) is captured once per step parity into CUDA graphs:
+//   pre:  cell lists -> contacts -> incidence -> SPOOK rows + warm start -> v^0
+//   jac:  N_it projected Jacobi sweeps
+//   post: integration, geometry forces, kinematic geometry
+// A Morton re-sort graph runs before every `resort_every`-th step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dem_internal.cuh"
+
+static thread_local std::string g_err;
+
+static dem_status fail(dem_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(DEM_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                             \
+    } while (0)
+
+struct dem_bed {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    SimParams P{};
+    DevBuf B{};
+    int resort_every = 20;
+    int64_t steps = 0;
+    bool faulted = false;
+    dem_alloc_fn alloc = nullptr;
+    dem_free_fn freef = nullptr;
+    void* actx = nullptr;
+    std::vector<void*> allocs;
+    int n_geom = 0;
+    std::vector<double> z_ref;  // particle surface under each primitive at creation
+    // graphs: [parity][pre, jac, post]
+    cudaGraphExec_t g[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    cudaGraphExec_t g_resort = nullptr;
+    int k_step = 0, k_resort = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<cudaEvent_t> ev_used;   // 4 per timed step: start, Jacobi start, Jacobi end, end
+    double t_step_ms = 0, t_jac_ms = 0;
+    int64_t t_steps = 0;
+};
+
+// ---------------------------------------------------------------------------
+// memory
+// ---------------------------------------------------------------------------
+static dem_status dalloc(dem_bed* b, void** p, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 256);
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (b->alloc) {
+        *p = b->alloc(bytes, b->actx, (void*)b->stream);
+        if (!*p) return fail(DEM_ERR_CUDA, "allocator callback returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync(p, bytes, b->stream);
+        if (e != cudaSuccess)
+            return fail(DEM_ERR_CUDA, "cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b->allocs.push_back(*p);
+    return DEM_OK;
+}
+
+template <typename T>
+static dem_status dalloc_n(dem_bed* b, T** p, size_t count) {
+    return dalloc(b, (void**)p, count * sizeof(T));
+}
+
+static void release(dem_bed* b) {
+    if (!b) return;
+    cudaSetDevice(b->dev);
+    cudaStreamSynchronize(b->stream);
+    for (int p = 0; p < 2; ++p)
+        for (int k = 0; k < 3; ++k)
+            if (b->g[p][k]) cudaGraphExecDestroy(b->g[p][k]);
+    if (b->g_resort) cudaGraphExecDestroy(b->g_resort);
+    for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_used) cudaEventDestroy(e);
+    for (void* p : b->allocs) {
+        if (b->freef) b->freef(p, b->actx, (void*)b->stream);
+        else cudaFreeAsync(p, b->stream);
+    }
+    cudaStreamSynchronize(b->stream);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// ---------------------------------------------------------------------------
+// creation
+// ---------------------------------------------------------------------------
+static double estar(double E1, double nu1, double E2, double nu2) {
+    return 1.0 / ((1.0 - nu1 * nu1) / E1 + (1.0 - nu2 * nu2) / E2);
+}
+
+static dem_status build_graphs(dem_bed* b);
+
+extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_bed** out) {
+    g_err.clear();
+    if (!out) return fail(DEM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(DEM_ERR_ARG, "desc is NULL");
+    const int n = d->n;
+    if (n < 0) return fail(DEM_ERR_ARG, "n = %d < 0", n);
+    if (n > 0 && (!d->pos || !d->radius)) return fail(DEM_ERR_ARG, "pos and radius are required");
+    if (d->n_geom < 0 || d->n_geom > DEM_MAX_GEOM)
+        return fail(DEM_ERR_ARG, "n_geom = %d outside [0, %d]", d->n_geom, DEM_MAX_GEOM);
+    if (d->n_geom > 0 && !d->geom) return fail(DEM_ERR_ARG, "geom is NULL");
+    if (!(d->dt > 0.f)) return fail(DEM_ERR_ARG, "dt must be > 0");
+    if (d->n_it < 0) return fail(DEM_ERR_ARG, "n_it < 0");
+    if (!(d->E > 0.f) || !(d->nu > -1.f && d->nu < 0.5f)) return fail(DEM_ERR_ARG, "bad E or nu");
+    if (!(d->e_H >= 1.f)) return fail(DEM_ERR_ARG, "e_H must be >= 1");
+    if (!(d->rho > 0.f) && !(d->inv_mass && d->inv_inertia)) return fail(DEM_ERR_ARG, "rho must be > 0");
+    if (d->damp_steps < 0.f || d->mu_t < 0.f || d->mu_r < 0.f || d->eps_reg < 0.f)
+        return fail(DEM_ERR_ARG, "negative damping, friction or regularisation");
+    for (int g = 0; g < d->n_geom; ++g) {
+        const dem_geom& G = d->geom[g];
+        if (G.type < 0 || G.type > 2) return fail(DEM_ERR_ARG, "geom %d: bad type %d", g, G.type);
+        if (!(G.E > 0.f) || G.mu_t < 0.f || G.mu_r < 0.f) return fail(DEM_ERR_ARG, "geom %d: bad material", g);
+    }
+
+    dem_bed* b = new dem_bed();
+    cudaGetDevice(&b->dev);
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return fail(DEM_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        b->own_stream = true;
+    }
+    b->alloc = d->alloc;
+    b->freef = d->free_fn;
+    b->actx = d->alloc_ctx;
+    if ((b->alloc == nullptr) != (b->freef == nullptr)) {
+        release(b);
+        return fail(DEM_ERR_ARG, "alloc and free_fn must be given together");
+    }
+    b->resort_every = d->resort_every > 0 ? d->resort_every : 20;
+    b->n_geom = d->n_geom;
+
+    // host copies of the inputs (they may live on the device)
+    std::vector<double> pos(3 * (size_t)n);
+    std::vector<float> rad(n), vel(3 * (size_t)n, 0.f), omg(3 * (size_t)n, 0.f), im(n), iI(n);
+    auto fetch = [&](void* dst, const void* src, size_t bytes) -> bool {
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyDefault) == cudaSuccess;
+    };
+    if (n > 0) {
+        bool ok = fetch(pos.data(), d->pos, pos.size() * 8) && fetch(rad.data(), d->radius, rad.size() * 4);
+        if (d->vel) ok = ok && fetch(vel.data(), d->vel, vel.size() * 4);
+        if (d->omega) ok = ok && fetch(omg.data(), d->omega, omg.size() * 4);
+        if (d->inv_mass) ok = ok && fetch(im.data(), d->inv_mass, im.size() * 4);
+        if (d->inv_inertia) ok = ok && fetch(iI.data(), d->inv_inertia, iI.size() * 4);
+        if (!ok) {
+            release(b);
+            return fail(DEM_ERR_ARG, "could not read the input arrays");
+        }
+    }
+    double rmin = 1e300, rmaxg = 0.0;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < n; ++i) {
+        if (!(rad[i] > 0.f) || !std::isfinite(rad[i])) {
+            release(b);
+            return fail(DEM_ERR_ARG, "radius[%d] = %g is not positive", i, (double)rad[i]);
+        }
+        for (int k = 0; k < 3; ++k) {
+            if (!std::isfinite(pos[3 * i + k])) {
+                release(b);
+                return fail(DEM_ERR_ARG, "pos[%d] is not finite", i);
+            }
+            lo[k] = std::min(lo[k], pos[3 * i + k]);
+            hi[k] = std::max(hi[k], pos[3 * i + k]);
+        }
+        rmin = std::min(rmin, (double)rad[i]);
+        rmaxg = std::max(rmaxg, (double)rad[i]);
+        const double m = (double)d->rho * 4.0 / 3.0 * M_PI * rad[i] * rad[i] * rad[i];
+        if (!d->inv_mass) im[i] = (float)(1.0 / m);
+        if (!d->inv_inertia) iI[i] = (float)(1.0 / (0.4 * m * rad[i] * rad[i]));
+    }
+    if (n == 0) { rmin = rmaxg = 1e-3; for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = 0; } }
+
+    // radius bands: level k holds rmin * ratio^k <= r < rmin * ratio^(k+1)
+    const double ratio = d->level_ratio > 1.f ? d->level_ratio : 2.0;
+    std::vector<int> lvl(n, 0);
+    int lmax = 0;
+    for (int i = 0; i < n; ++i) {
+        int k = 0;
+        double edge = rmin * ratio;
+        while (k < DEM_MAX_LEVELS - 1 && (double)rad[i] >= edge) { ++k; edge *= ratio; }
+        lvl[i] = k;
+        lmax = std::max(lmax, k);
+    }
+    // drop empty levels
+    std::vector<int> remap(lmax + 1, -1);
+    std::vector<double> lev_rmax;
+    {
+        std::vector<int> used(lmax + 1, 0);
+        for (int i = 0; i < n; ++i) used[lvl[i]] = 1;
+        if (n == 0) used[0] = 1;
+        for (int k = 0; k <= lmax; ++k)
+            if (used[k]) { remap[k] = (int)lev_rmax.size(); lev_rmax.push_back(0.0); }
+        for (int i = 0; i < n; ++i) {
+            lvl[i] = remap[lvl[i]];
+            lev_rmax[lvl[i]] = std::max(lev_rmax[lvl[i]], (double)rad[i]);
+        }
+        if (n == 0) lev_rmax[0] = rmaxg;
+    }
+    const int L = (int)lev_rmax.size();
+
+    SimParams& P = b->P;
+    P.n = n;
+    P.ng = d->n_geom;
+    P.n_levels = L;
+    P.n_it = d->n_it;
+    P.dt = d->dt;
+    P.inv_dt = 1.0f / d->dt;
+    P.e_H = d->e_H;
+    P.kn_scale = d->kn_scale > 0.f ? d->kn_scale : 1.0f;
+    P.eps_reg = d->eps_reg;
+    P.delta_floor = d->delta_floor > 0.f ? d->delta_floor : (float)(1e-6 * 2.0 * rmin);
+    P.ups = 1.0f / (1.0f + 4.0f * d->damp_steps);
+    P.Estar_ss = (float)estar(d->E, d->nu, d->E, d->nu);
+    P.mu_t = d->mu_t;
+    P.mu_r = d->mu_r;
+    P.gx = d->gravity[0]; P.gy = d->gravity[1]; P.gz = d->gravity[2];
+    int64_t cap = d->contact_capacity > 0 ? d->contact_capacity : 8LL * n + 1024;
+    if (cap > (int64_t)0x3fffffff) cap = 0x3fffffff;
+    P.max_contacts = (int)cap;
+    P.max_geo = 2 * n + 1024;
+
+    // grids over the particle bounding box plus a margin
+    double ext = 0.0, absmax = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        ext = std::max(ext, hi[k] - lo[k]);
+        absmax = std::max(absmax, std::max(std::fabs(lo[k]), std::fabs(hi[k])));
+    }
+    const double margin = std::max(4.0 * rmaxg, 0.05 * ext);
+    // FP32 rounding of the copies: <= 2^-24 |x| per coordinate
+    P.tol = (float)(4.0 * std::ldexp(absmax + margin, -23) + 8.0 * std::ldexp(2.0 * rmaxg, -24));
+    int64_t total_cells = 0;
+    for (int l = 0; l < L; ++l) {
+        LevelGrid& g = P.lv[l];
+        double cell = 2.0 * lev_rmax[l] * (1.0 + 1e-4) + 2.0 * P.tol;
+        int dims[3];
+        for (;;) {
+            int64_t c = 1;
+            for (int k = 0; k < 3; ++k) {
+                dims[k] = std::max(1, (int)std::ceil((hi[k] - lo[k] + 2 * margin) / cell));
+                c *= dims[k];
+            }
+            if (c <= (int64_t)(48 << 20)) break;
+            cell *= 1.25;   // cap the cell count; larger cells stay correct
+        }
+        g.ox = (float)(lo[0] - margin);
+        g.oy = (float)(lo[1] - margin);
+        g.oz = (float)(lo[2] - margin);
+        g.cell = (float)cell;
+        g.inv_cell = (float)(1.0 / cell);
+        g.nx = dims[0]; g.ny = dims[1]; g.nz = dims[2];
+        g.offset = (int)total_cells;
+        g.rmax = (float)lev_rmax[l];
+        total_cells += (int64_t)dims[0] * dims[1] * dims[2];
+    }
+    if (total_cells > (int64_t)(200 << 20)) {
+        release(b);
+        return fail(DEM_ERR_ARG, "broad-phase grids need %lld cells", (long long)total_cells);
+    }
+    P.n_cells = (int)total_cells;
+
+    // sinkage references: highest particle top under each primitive's footprint
+    b->z_ref.assign(P.ng, 0.0);
+    double ztop_all = -1e300;
+    for (int i = 0; i < n; ++i) ztop_all = std::max(ztop_all, pos[3 * i + 2] + rad[i]);
+    for (int g = 0; g < P.ng; ++g) {
+        const dem_geom& G = d->geom[g];
+        double zr = -1e300;
+        for (int i = 0; i < n; ++i) {
+            const double dx = pos[3 * i] - G.c[0], dy = pos[3 * i + 1] - G.c[1];
+            bool under = false;
+            if (G.type == DEM_GEOM_CYLINDER) under = dx * dx + dy * dy <= G.he[0] * G.he[0];
+            else if (G.type == DEM_GEOM_BOX) {
+                double ex = 0, ey = 0;
+                for (int k = 0; k < 3; ++k) {
+                    ex += std::fabs(G.R[k]) * G.he[k];
+                    ey += std::fabs(G.R[3 + k]) * G.he[k];
+                }
+                under = std::fabs(dx) <= ex && std::fabs(dy) <= ey;
+            }
+            if (under) zr = std::max(zr, pos[3 * i + 2] + rad[i]);
+        }
+        b->z_ref[g] = zr > -1e299 ? zr : ztop_all;
+    }
+
+    // ---- device memory ----
+    DevBuf& B = b->B;
+    const size_t N = std::max(n, 1), C = (size_t)P.max_contacts, GC = (size_t)P.max_geo;
+    const size_t NC = (size_t)P.n_cells;
+    const int nbr = radix_blocks(n);
+    dem_status st = DEM_OK;
+#define AL(ptr, cnt) if (st == DEM_OK) st = dalloc_n(b, &(ptr), (cnt))
+    AL(B.pos, N); AL(B.posr, N); AL(B.vel0, N); AL(B.omg0, N);
+    AL(B.vel[0], N); AL(B.vel[1], N); AL(B.omg[0], N); AL(B.omg[1], N);
+    AL(B.id, N); AL(B.lvl, N); AL(B.prev_of, N); AL(B.resorted, 1); AL(B.err, 1);
+    AL(B.body_cell, N); AL(B.cell_cnt, NC + 1); AL(B.cell_start, NC + 1); AL(B.cell_fill, NC + 1);
+    AL(B.cell_body, N);
+    AL(B.tmp_own, N * DEM_MAX_OWN); AL(B.tmp_geo, N * DEM_MAX_GEO);
+    AL(B.own_cnt, N + 1); AL(B.in_cnt, N + 1); AL(B.geo_cnt, N + 1); AL(B.in_fill, N + 1);
+    AL(B.own_start[0], N + 1); AL(B.own_start[1], N + 1); AL(B.inc_start, N + 1);
+    AL(B.geo_start[0], N + 1); AL(B.geo_start[1], N + 1);
+    AL(B.c_other, C); AL(B.c_key[0], C); AL(B.c_key[1], C); AL(B.rec, 3 * C); AL(B.c_delta, C);
+    AL(B.lamA[0], C); AL(B.lamA[1], C); AL(B.lamB[0], C); AL(B.lamB[1], C);
+    AL(B.lamW[0], 2 * C); AL(B.lamW[1], 2 * C); AL(B.inc, 2 * C);
+    AL(B.g_key[0], GC); AL(B.g_key[1], GC); AL(B.grec, 6 * GC); AL(B.g_delta, GC);
+    AL(B.glamA[0], GC); AL(B.glamA[1], GC); AL(B.glamB[0], GC); AL(B.glamB[1], GC);
+    AL(B.glamW[0], 2 * GC); AL(B.glamW[1], 2 * GC);
+    AL(B.geom, (size_t)std::max(P.ng, 1)); AL(B.gacc, 6 * (size_t)std::max(P.ng, 1));
+    AL(B.key_a, N); AL(B.key_b, N); AL(B.val_a, N); AL(B.val_b, N);
+    AL(B.hist, 256 * (size_t)nbr + 1);
+    AL(B.t_pos, N); AL(B.t_v, N); AL(B.t_w, N); AL(B.t_id, N); AL(B.t_lvl, N);
+    // scan scratch: tile totals of up to 3 columns over the largest scanned array
+    const size_t scan_n = std::max({NC + 1, N + 1, 256 * (size_t)nbr + 1});
+    AL(B.scan_tmp, 3 * (scan_n / 2048 + 2));
+#undef AL
+    if (st != DEM_OK) {
+        release(b);
+        return st;
+    }
+
+    // ---- upload ----
+    std::vector<double4_32a> hp(N);
+    std::vector<float4> hr(N), hv(N), hw(N);
+    std::vector<int> hid(N), hl(N);
+    for (int i = 0; i < n; ++i) {
+        hp[i] = make_double4_32a(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], (double)rad[i]);
+        hr[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], rad[i]);
+        hv[i] = make_float4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], im[i]);
+        hw[i] = make_float4(omg[3 * i], omg[3 * i + 1], omg[3 * i + 2], iI[i]);
+        hid[i] = i;
+        hl[i] = lvl[i];
+    }
+    std::vector<GeomDev> hg(std::max(P.ng, 1));
+    for (int g = 0; g < P.ng; ++g) {
+        const dem_geom& G = d->geom[g];
+        GeomDev& o = hg[g];
+        memset(&o, 0, sizeof o);
+        for (int k = 0; k < 3; ++k) { o.c[k] = G.c[k]; o.he[k] = G.he[k]; o.v[k] = G.v[k]; o.w[k] = G.w[k]; }
+        for (int k = 0; k < 9; ++k) o.R[k] = G.R[k];
+        o.type = G.type;
+        o.Estar = (float)estar(d->E, d->nu, G.E, G.nu);
+        o.mu_t = G.mu_t;
+        o.mu_r = G.mu_r;
+        o.bound = (float)(G.type == DEM_GEOM_BOX ? std::sqrt(G.he[0] * G.he[0] + G.he[1] * G.he[1] + G.he[2] * G.he[2])
+                                                 : std::sqrt(G.he[0] * G.he[0] + G.he[2] * G.he[2])) * 1.0001f;
+    }
+    cudaStream_t s = b->stream;
+    CK(cudaMemcpyAsync(B.pos, hp.data(), N * sizeof(double4_32a), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.posr, hr.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.vel0, hv.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.omg0, hw.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.id, hid.data(), N * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.lvl, hl.data(), N * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.geom, hg.data(), hg.size() * sizeof(GeomDev), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(B.own_start[0], 0, (N + 1) * sizeof(int), s));
+    CK(cudaMemsetAsync(B.own_start[1], 0, (N + 1) * sizeof(int), s));
+    CK(cudaMemsetAsync(B.geo_start[0], 0, (N + 1) * sizeof(int), s));
+    CK(cudaMemsetAsync(B.geo_start[1], 0, (N + 1) * sizeof(int), s));
+    CK(cudaMemsetAsync(B.inc_start, 0, (N + 1) * sizeof(int), s));
+    CK(cudaMemsetAsync(B.err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(B.resorted, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(B.gacc, 0, 6 * std::max(P.ng, 1) * sizeof(long long), s));
+    CK(cudaStreamSynchronize(s));
+
+    st = build_graphs(b);
+    if (st != DEM_OK) {
+        std::string keep = g_err;
+        release(b);
+        g_err = keep;
+        return st;
+    }
+    *out = b;
+    return DEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// graphs
+// ---------------------------------------------------------------------------
+static dem_status capture(dem_bed* b, cudaGraphExec_t* exec, int* kernels,
+                          int (*body)(dem_bed*, int), int arg) {
+    cudaStream_t s = b->stream;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int k = body(b, arg);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (le != cudaSuccess) return fail(DEM_ERR_CUDA, "kernel launch during capture: %s", cudaGetErrorString(le));
+    if (e != cudaSuccess) return fail(DEM_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(DEM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    if (kernels) *kernels += k;
+    return DEM_OK;
+}
+
+static int body_pre(dem_bed* b, int p) {
+    const SimParams& P = b->P;
+    const DevBuf& B = b->B;
+    cudaStream_t s = b->stream;
+    const size_t N = std::max(P.n, 1);
+    int k = 0;
+    cudaMemsetAsync(B.cell_cnt, 0, ((size_t)P.n_cells + 1) * sizeof(int), s);
+    cudaMemsetAsync(B.cell_fill, 0, ((size_t)P.n_cells + 1) * sizeof(int), s);
+    cudaMemsetAsync(B.in_cnt, 0, (N + 1) * sizeof(int), s);
+    cudaMemsetAsync(B.in_fill, 0, (N + 1) * sizeof(int), s);
+    cudaMemsetAsync(B.gacc, 0, 6 * std::max(P.ng, 1) * sizeof(long long), s);
+    if (P.n == 0) {
+        cudaMemsetAsync(B.own_start[p], 0, sizeof(int), s);
+        cudaMemsetAsync(B.geo_start[p], 0, sizeof(int), s);
+        cudaMemsetAsync(B.inc_start, 0, sizeof(int), s);
+        return 0;
+    }
+    k += launch_cell_count(P, B, s);
+    k += launch_scan(B.cell_cnt, B.cell_start, P.n_cells, B.scan_tmp, s);
+    k += launch_cell_fill(P, B, s);
+    k += launch_pairs(P, B, s);
+    k += launch_scan3(B.own_cnt, B.own_cnt, B.in_cnt, B.geo_cnt, B.own_start[p], B.inc_start,
+                      B.geo_start[p], P.n, B.scan_tmp, s);
+    k += launch_contacts_build(P, B, p, s);
+    k += launch_inc_sort(P, B, s);
+    k += launch_setup(P, B, p, s);
+    k += launch_v0(P, B, p, s);
+    return k;
+}
+
+static int body_jac(dem_bed* b, int p) {
+    int k = 0;
+    if (b->P.n == 0) return 0;
+    for (int it = 0; it < b->P.n_it; ++it) k += launch_jacobi(b->P, b->B, p, it, b->stream);
+    return k;
+}
+
+static int body_post(dem_bed* b, int p) {
+    if (b->P.n == 0) return 0;
+    return launch_integrate(b->P, b->B, p, b->stream);
+}
+
+static int body_resort(dem_bed* b, int) { return launch_resort(b->P, b->B, b->stream); }
+
+static dem_status build_graphs(dem_bed* b) {
+    dem_status st;
+    for (int p = 0; p < 2; ++p) {
+        int k = 0;
+        if ((st = capture(b, &b->g[p][0], &k, body_pre, p)) != DEM_OK) return st;
+        if (b->P.n_it > 0 && b->P.n > 0) {
+            if ((st = capture(b, &b->g[p][1], &k, body_jac, p)) != DEM_OK) return st;
+        }
+        if (b->P.n > 0) {
+            if ((st = capture(b, &b->g[p][2], &k, body_post, p)) != DEM_OK) return st;
+        }
+        b->k_step = k;
+    }
+    int kr = 0;
+    if (b->P.n > 1) {
+        if ((st = capture(b, &b->g_resort, &kr, body_resort, 0)) != DEM_OK) return st;
+    }
+    b->k_resort = kr;
+    return DEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stepping and read-back
+// ---------------------------------------------------------------------------
+static cudaEvent_t take_event(dem_bed* b) {
+    cudaEvent_t e;
+    if (!b->ev_pool.empty()) {
+        e = b->ev_pool.back();
+        b->ev_pool.pop_back();
+    } else {
+        cudaEventCreate(&e);
+    }
+    b->ev_used.push_back(e);
+    return e;
+}
+
+// fold finished timing events into the sums (call after a synchronisation)
+static void collect_timing(dem_bed* b) {
+    for (size_t k = 0; k + 4 <= b->ev_used.size(); k += 4) {
+        float a = 0, j = 0;
+        cudaEventElapsedTime(&a, b->ev_used[k], b->ev_used[k + 3]);
+        cudaEventElapsedTime(&j, b->ev_used[k + 1], b->ev_used[k + 2]);
+        b->t_step_ms += a;
+        b->t_jac_ms += j;
+        b->t_steps += 1;
+    }
+    for (cudaEvent_t e : b->ev_used) b->ev_pool.push_back(e);
+    b->ev_used.clear();
+}
+
+static dem_status check_fault(dem_bed* b) {
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, b->B.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (b->timing) collect_timing(b);
+    if (err) {
+        b->faulted = true;
+        if (err & DEM_FLAG_CAPACITY)
+            return fail(DEM_ERR_CAPACITY, "contact storage overflowed (capacity %d contacts, %d per body)",
+                        b->P.max_contacts, DEM_MAX_OWN);
+        return fail(DEM_ERR_NONFINITE, "non-finite velocity");
+    }
+    return DEM_OK;
+}
+
+extern "C" dem_status dem_step(dem_bed* b, int32_t nsteps) {
+    g_err.clear();
+    if (!b) return fail(DEM_ERR_ARG, "bed is NULL");
+    if (nsteps < 0) return fail(DEM_ERR_ARG, "nsteps < 0");
+    if (b->faulted) return fail(DEM_ERR_STATE, "the bed holds a latched device fault");
+    CK(cudaSetDevice(b->dev));
+    for (int k = 0; k < nsteps; ++k) {
+        const bool resort = b->g_resort && b->steps % b->resort_every == 0;
+        const int p = (int)(b->steps & 1);
+        if (b->timing) {
+            if (b->ev_used.size() >= 4096) {
+                CK(cudaStreamSynchronize(b->stream));
+                collect_timing(b);
+            }
+            CK(cudaEventRecord(take_event(b), b->stream));
+            if (resort) CK(cudaGraphLaunch(b->g_resort, b->stream));
+            CK(cudaGraphLaunch(b->g[p][0], b->stream));
+            CK(cudaEventRecord(take_event(b), b->stream));
+            if (b->g[p][1]) CK(cudaGraphLaunch(b->g[p][1], b->stream));
+            CK(cudaEventRecord(take_event(b), b->stream));
+            if (b->g[p][2]) CK(cudaGraphLaunch(b->g[p][2], b->stream));
+            CK(cudaEventRecord(take_event(b), b->stream));
+        } else {
+            if (resort) CK(cudaGraphLaunch(b->g_resort, b->stream));
+            CK(cudaGraphLaunch(b->g[p][0], b->stream));
+            if (b->g[p][1]) CK(cudaGraphLaunch(b->g[p][1], b->stream));
+            if (b->g[p][2]) CK(cudaGraphLaunch(b->g[p][2], b->stream));
+        }
+        b->steps++;
+    }
+    return DEM_OK;
+}
+
+extern "C" dem_status dem_apply_plate_velocity(dem_bed* b, int32_t g, const double v[3], const double w[3]) {
+    g_err.clear();
+    if (!b || !v || !w) return fail(DEM_ERR_ARG, "NULL argument");
+    if (g < 0 || g >= b->n_geom) return fail(DEM_ERR_ARG, "geom %d out of range", g);
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(v[k]) || !std::isfinite(w[k])) return fail(DEM_ERR_ARG, "non-finite velocity");
+    CK(cudaSetDevice(b->dev));
+    double vw[6] = {v[0], v[1], v[2], w[0], w[1], w[2]};
+    // v and w are adjacent in GeomDev; a pageable source is staged before return
+    CK(cudaMemcpyAsync(&b->B.geom[g].v[0], vw, 6 * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    return DEM_OK;
+}
+
+static double z_bottom(const GeomDev& G) {
+    if (G.type == DEM_GEOM_BOX)
+        return G.c[2] - (std::fabs(G.R[6]) * G.he[0] + std::fabs(G.R[7]) * G.he[1] + std::fabs(G.R[8]) * G.he[2]);
+    if (G.type == DEM_GEOM_CYLINDER) {
+        const double az = std::fabs(G.R[8]);
+        return G.c[2] - (az * G.he[2] + G.he[0] * std::sqrt(std::max(0.0, 1.0 - az * az)));
+    }
+    return G.c[2];
+}
+
+extern "C" dem_status dem_read_forces(dem_bed* b, int32_t g, double f[3], double t[3], double* sinkage) {
+    g_err.clear();
+    if (!b) return fail(DEM_ERR_ARG, "bed is NULL");
+    if (g < 0 || g >= b->n_geom) return fail(DEM_ERR_ARG, "geom %d out of range", g);
+    CK(cudaSetDevice(b->dev));
+    long long acc[6];
+    GeomDev G;
+    CK(cudaMemcpyAsync(acc, b->B.gacc + 6 * g, sizeof acc, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(&G, b->B.geom + g, sizeof G, cudaMemcpyDeviceToHost, b->stream));
+    dem_status st = check_fault(b);
+    if (st != DEM_OK) return st;
+    const double sc = 1.0 / (DEM_FIX_SCALE * (double)b->P.dt);
+    for (int k = 0; k < 3; ++k) {
+        if (f) f[k] = (double)acc[k] * sc;
+        if (t) t[k] = (double)acc[3 + k] * sc;
+    }
+    if (sinkage) *sinkage = b->z_ref[g] - z_bottom(G);
+    return DEM_OK;
+}
+
+extern "C" dem_status dem_read_geom(dem_bed* b, int32_t g, dem_geom* out) {
+    g_err.clear();
+    if (!b || !out) return fail(DEM_ERR_ARG, "NULL argument");
+    if (g < 0 || g >= b->n_geom) return fail(DEM_ERR_ARG, "geom %d out of range", g);
+    CK(cudaSetDevice(b->dev));
+    GeomDev G;
+    CK(cudaMemcpyAsync(&G, b->B.geom + g, sizeof G, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    out->type = G.type;
+    for (int k = 0; k < 3; ++k) { out->c[k] = G.c[k]; out->he[k] = G.he[k]; out->v[k] = G.v[k]; out->w[k] = G.w[k]; }
+    for (int k = 0; k < 9; ++k) out->R[k] = G.R[k];
+    out->mu_t = G.mu_t;
+    out->mu_r = G.mu_r;
+    out->E = 0.f;
+    out->nu = 0.f;
+    return DEM_OK;
+}
+
+template <typename T>
+static dem_status copy_out(void* dst, const T* src, size_t count) {
+    // the caller's buffer may be host or device memory
+    CK(cudaMemcpy(dst, src, count * sizeof(T), cudaMemcpyDefault));
+    return DEM_OK;
+}
+
+extern "C" dem_status dem_read_state(dem_bed* b, double* pos, float* vel, float* omega, int32_t cap) {
+    g_err.clear();
+    if (!b) return fail(DEM_ERR_ARG, "bed is NULL");
+    const int n = b->P.n;
+    if (cap < n) return fail(DEM_ERR_ARG, "cap %d < n %d", cap, n);
+    CK(cudaSetDevice(b->dev));
+    if (n == 0) return check_fault(b);
+    std::vector<double4_32a> hp(n);
+    std::vector<float4> hv(n), hw(n);
+    std::vector<int> hid(n);
+    cudaStream_t s = b->stream;
+    CK(cudaMemcpyAsync(hp.data(), b->B.pos, n * sizeof(double4_32a), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hv.data(), b->B.vel0, n * sizeof(float4), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hw.data(), b->B.omg0, n * sizeof(float4), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hid.data(), b->B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    dem_status st = check_fault(b);
+    if (st != DEM_OK) return st;
+    std::vector<double> op(3 * (size_t)n);
+    std::vector<float> ov(3 * (size_t)n), ow(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const int k = hid[i];
+        op[3 * k] = hp[i].x; op[3 * k + 1] = hp[i].y; op[3 * k + 2] = hp[i].z;
+        ov[3 * k] = hv[i].x; ov[3 * k + 1] = hv[i].y; ov[3 * k + 2] = hv[i].z;
+        ow[3 * k] = hw[i].x; ow[3 * k + 1] = hw[i].y; ow[3 * k + 2] = hw[i].z;
+    }
+    if (pos && (st = copy_out(pos, op.data(), op.size())) != DEM_OK) return st;
+    if (vel && (st = copy_out(vel, ov.data(), ov.size())) != DEM_OK) return st;
+    if (omega && (st = copy_out(omega, ow.data(), ow.size())) != DEM_OK) return st;
+    return DEM_OK;
+}
+
+extern "C" dem_status dem_read_contacts(dem_bed* b, int64_t cap, int32_t* key_a, int32_t* key_b,
+                                        float* lam7, float* delta, int64_t* count) {
+    g_err.clear();
+    if (!b || !count) return fail(DEM_ERR_ARG, "NULL argument");
+    if (cap < 0) return fail(DEM_ERR_ARG, "cap < 0");
+    CK(cudaSetDevice(b->dev));
+    *count = 0;
+    const int n = b->P.n;
+    if (b->steps == 0 || n == 0) return check_fault(b);
+    const int p = (int)((b->steps - 1) & 1);   // parity of the last step
+    cudaStream_t s = b->stream;
+    const DevBuf& B = b->B;
+    std::vector<int> os(n + 1), gs(n + 1), hid(n);
+    CK(cudaMemcpyAsync(os.data(), B.own_start[p], (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(gs.data(), B.geo_start[p], (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hid.data(), B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    dem_status st = check_fault(b);
+    if (st != DEM_OK) return st;
+    const int nc = os[n], ngc = gs[n];
+    std::vector<int> key(std::max(nc, 1)), gk(std::max(ngc, 1));
+    std::vector<float4> lw(2 * (size_t)std::max(nc, 1)), glw(2 * (size_t)std::max(ngc, 1));
+    std::vector<float> dl(std::max(nc, 1)), gdl(std::max(ngc, 1));
+    if (nc > 0) {
+        CK(cudaMemcpyAsync(key.data(), B.c_key[p], nc * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(lw.data(), B.lamW[p], 2 * (size_t)nc * sizeof(float4), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(dl.data(), B.c_delta, nc * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    if (ngc > 0) {
+        CK(cudaMemcpyAsync(gk.data(), B.g_key[p], ngc * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(glw.data(), B.glamW[p], 2 * (size_t)ngc * sizeof(float4), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(gdl.data(), B.g_delta, ngc * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    const int64_t total = (int64_t)nc + ngc;
+    *count = total;
+    std::vector<int32_t> ka(total), kb(total);
+    std::vector<float> l7(7 * (size_t)total), d7(total);
+    int64_t m = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int c = os[i]; c < os[i + 1]; ++c, ++m) {
+            ka[m] = hid[i]; kb[m] = key[c]; d7[m] = dl[c];
+            const float4 a = lw[2 * (size_t)c], q = lw[2 * (size_t)c + 1];
+            const float v[7] = {a.x, a.y, a.z, a.w, q.x, q.y, q.z};
+            memcpy(&l7[7 * m], v, sizeof v);
+        }
+        for (int c = gs[i]; c < gs[i + 1]; ++c, ++m) {
+            ka[m] = hid[i]; kb[m] = -(gk[c] + 1); d7[m] = gdl[c];
+            const float4 a = glw[2 * (size_t)c], q = glw[2 * (size_t)c + 1];
+            const float v[7] = {a.x, a.y, a.z, a.w, q.x, q.y, q.z};
+            memcpy(&l7[7 * m], v, sizeof v);
+        }
+    }
+    const int64_t w = std::min<int64_t>(cap, total);
+    if (w > 0) {
+        if (key_a && (st = copy_out(key_a, ka.data(), w)) != DEM_OK) return st;
+        if (key_b && (st = copy_out(key_b, kb.data(), w)) != DEM_OK) return st;
+        if (lam7 && (st = copy_out(lam7, l7.data(), 7 * w)) != DEM_OK) return st;
+        if (delta && (st = copy_out(delta, d7.data(), w)) != DEM_OK) return st;
+    }
+    return DEM_OK;
+}
+
+extern "C" dem_status dem_sync(dem_bed* b) {
+    g_err.clear();
+    if (!b) return fail(DEM_ERR_ARG, "bed is NULL");
+    CK(cudaSetDevice(b->dev));
+    return check_fault(b);
+}
+
+extern "C" dem_status dem_get_info(dem_bed* b, dem_info* out) {
+    g_err.clear();
+    if (!b || !out) return fail(DEM_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(b->dev));
+    memset(out, 0, sizeof *out);
+    out->n = b->P.n;
+    out->n_levels = b->P.n_levels;
+    out->n_cells = b->P.n_cells;
+    out->steps = b->steps;
+    out->contact_capacity = b->P.max_contacts;
+    out->kernels_per_step = b->k_step;
+    out->kernels_per_resort = b->k_resort;
+    if (b->steps > 0 && b->P.n > 0) {
+        const int p = (int)((b->steps - 1) & 1);
+        int a = 0, g = 0;
+        CK(cudaMemcpyAsync(&a, b->B.own_start[p] + b->P.n, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaMemcpyAsync(&g, b->B.geo_start[p] + b->P.n, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        out->contacts = a;
+        out->geom_contacts = g;
+    }
+    return check_fault(b);
+}
+
+extern "C" dem_status dem_set_timing(dem_bed* b, int32_t enable) {
+    g_err.clear();
+    if (!b) return fail(DEM_ERR_ARG, "bed is NULL");
+    CK(cudaSetDevice(b->dev));
+    CK(cudaStreamSynchronize(b->stream));
+    collect_timing(b);
+    b->timing = enable != 0;
+    b->t_step_ms = b->t_jac_ms = 0;
+    b->t_steps = 0;
+    return DEM_OK;
+}
+
+extern "C" dem_status dem_read_timing(dem_bed* b, double* step_ms, double* jacobi_ms, int64_t* steps) {
+    g_err.clear();
+    if (!b) return fail(DEM_ERR_ARG, "bed is NULL");
+    CK(cudaSetDevice(b->dev));
+    CK(cudaStreamSynchronize(b->stream));
+    collect_timing(b);
+    if (step_ms) *step_ms = b->t_step_ms;
+    if (jacobi_ms) *jacobi_ms = b->t_jac_ms;
+    if (steps) *steps = b->t_steps;
+    return DEM_OK;
+}
+
+extern "C" dem_status dem_destroy_bed(dem_bed* b) {
+    g_err.clear();
+    release(b);
+    return DEM_OK;
+}
+
+extern "C" const char* dem_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,207 @@
+// Broad and narrow phase: multi-level cell lists, sphere-sphere and
+// sphere-geometry contact detection, contact and incidence lists.
+//
+// Levels: every particle belongs to one radius band ("level"); the cells of
+// level l are 2 r_max(l) wide.  Two particles of the same level that touch lie
+// in neighbouring cells; a particle looks for partners of a coarser level l'
+// in the 27 cells of level l' around it, since r_a + r_b <= 2 r_max(l').
+// A pair of the same level is owned by the lower stable id, a cross-level pair
+// by the finer particle, so every pair is found exactly once (Sec. 2.2: the
+// contact set is recomputed every time step).
+//
+// Contact predicate (exact): |x_a - x_b|^2 < (r_a + r_b)^2 evaluated in IEEE
+// double from the double centres, as (dx^2 + dy^2) + dz^2 with every product
+// and sum rounded separately (no fused multiply-add).  An FP32 pre-test with a
+// tolerance that covers the rounding of the FP32 copies rejects the far pairs.
+#include "dem_internal.cuh"
+
+#define BP_T 128
+
+#include "geometry.cuh"
+
+// FP32 pre-test: can the sphere touch the primitive at all?
+static __device__ __forceinline__ bool geom_near(const GeomDev& g, float4 p, float tol) {
+    float cx = (float)g.c[0], cy = (float)g.c[1], cz = (float)g.c[2];
+    float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
+    if (g.type == DEM_GEOM_PLANE) {
+        float s = (float)g.R[2] * dx + (float)g.R[5] * dy + (float)g.R[8] * dz;
+        return s < p.w + tol;
+    }
+    float reach = g.bound + p.w + tol;
+    return dx * dx + dy * dy + dz * dz < reach * reach;
+}
+
+// ---------------------------------------------------------------------------
+// cell lists (counting sort of particles by cell, rebuilt every step)
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ int cell_of(const LevelGrid& g, float4 p, int& cx, int& cy, int& cz) {
+    cx = cell_coord(p.x, g.ox, g.inv_cell, g.nx);
+    cy = cell_coord(p.y, g.oy, g.inv_cell, g.ny);
+    cz = cell_coord(p.z, g.oz, g.inv_cell, g.nz);
+    return g.offset + cx + g.nx * (cy + g.ny * cz);
+}
+
+__global__ void __launch_bounds__(BP_T) k_cell_count(SimParams P, DevBuf B) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    int cx, cy, cz;
+    int c = cell_of(P.lv[B.lvl[i]], B.posr[i], cx, cy, cz);
+    B.body_cell[i] = c;
+    atomicAdd(&B.cell_cnt[c], 1);
+}
+
+__global__ void __launch_bounds__(BP_T) k_cell_fill(SimParams P, DevBuf B) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    int c = B.body_cell[i];
+    int k = atomicAdd(&B.cell_fill[c], 1);
+    B.cell_body[B.cell_start[c] + k] = i;
+}
+
+// ---------------------------------------------------------------------------
+// narrow phase
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const float4 pi = B.posr[i];
+    const double4_32a xi = B.pos[i];
+    const int li = B.lvl[i];
+    const int idi = B.id[i];
+    int2* own = B.tmp_own + (size_t)i * DEM_MAX_OWN;
+    int nown = 0;
+    bool overflow = false;
+    for (int l = li; l < P.n_levels; ++l) {
+        const LevelGrid g = P.lv[l];
+        int cx, cy, cz;
+        cell_of(g, pi, cx, cy, cz);
+        const int z0 = max(cz - 1, 0), z1 = min(cz + 1, g.nz - 1);
+        const int y0 = max(cy - 1, 0), y1 = min(cy + 1, g.ny - 1);
+        const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
+        for (int z = z0; z <= z1; ++z)
+            for (int y = y0; y <= y1; ++y) {
+                const int row = g.offset + g.nx * (y + g.ny * z);
+                const int s = B.cell_start[row + x0], e = B.cell_start[row + x1 + 1];
+                for (int k = s; k < e; ++k) {
+                    const int j = B.cell_body[k];
+                    if (j == i) continue;
+                    const float4 pj = B.posr[j];
+                    const float R = pi.w + pj.w + P.tol;
+                    const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                    if (dx * dx + dy * dy + dz * dz >= R * R) continue;
+                    const int idj = B.id[j];
+                    if (l == li && idj < idi) continue;  // same level: the lower id owns
+                    if (!exact_pair(xi, B.pos[j])) continue;
+                    if (nown < DEM_MAX_OWN) {
+                        // insertion by the other body's stable id keeps the list sorted
+                        int q = nown;
+                        while (q > 0 && own[q - 1].y > idj) { own[q] = own[q - 1]; --q; }
+                        own[q] = make_int2(j, idj);
+                        ++nown;
+                        atomicAdd(&B.in_cnt[j], 1);
+                    } else {
+                        overflow = true;
+                    }
+                }
+            }
+    }
+    int ngeo = 0;
+    int* gl = B.tmp_geo + (size_t)i * DEM_MAX_GEO;
+    for (int gi = 0; gi < P.ng; ++gi) {
+        const GeomDev& g = B.geom[gi];
+        if (!geom_near(g, pi, P.tol)) continue;
+        GeoHit h = geom_hit(g, xi.x, xi.y, xi.z, xi.w);
+        if (!h.hit) continue;
+        if (ngeo < DEM_MAX_GEO) gl[ngeo++] = gi;
+        else overflow = true;
+    }
+    B.own_cnt[i] = nown;
+    B.geo_cnt[i] = ngeo;
+    if (overflow) set_flag(B.err, DEM_FLAG_CAPACITY);
+}
+
+// Owned lists -> contact arrays; both ends of every contact -> incidence lists.
+__global__ void __launch_bounds__(BP_T) k_contacts_build(SimParams P, DevBuf B, int parity) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const int os = B.own_start[parity][i];
+    const int no = B.own_cnt[i];
+    const int is = B.inc_start[i];
+    const int2* own = B.tmp_own + (size_t)i * DEM_MAX_OWN;
+    const long long inc_cap = 2LL * P.max_contacts;
+    for (int k = 0; k < no; ++k) {
+        const int c = os + k;
+        if (c >= P.max_contacts) { set_flag(B.err, DEM_FLAG_CAPACITY); break; }
+        const int2 e = own[k];
+        B.c_other[c] = e.x;
+        B.c_key[parity][c] = e.y;
+        if (is + k < inc_cap) B.inc[is + k] = make_int2(c, e.x);
+        const int slot = atomicAdd(&B.in_fill[e.x], 1);
+        const long long pos = (long long)B.inc_start[e.x] + B.own_cnt[e.x] + slot;
+        if (pos < inc_cap) B.inc[pos] = make_int2(c | (int)0x80000000, i);
+        else set_flag(B.err, DEM_FLAG_CAPACITY);
+    }
+    const int gs = B.geo_start[parity][i];
+    const int ng = B.geo_cnt[i];
+    const int* gl = B.tmp_geo + (size_t)i * DEM_MAX_GEO;
+    const int gcap = P.max_geo;
+    for (int k = 0; k < ng; ++k) {
+        if (gs + k >= gcap) { set_flag(B.err, DEM_FLAG_CAPACITY); break; }
+        B.g_key[parity][gs + k] = gl[k];
+    }
+}
+
+// Sort every incidence list by the stable id of the other body.
+__global__ void __launch_bounds__(BP_T) k_inc_sort(SimParams P, DevBuf B) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n || *B.err) return;
+    const int s = B.inc_start[i], e = B.inc_start[i + 1];
+    const int m = e - s;
+    const int no = B.own_cnt[i];
+    if (m - no <= 0) return;   // only owned entries, already sorted
+    int2* L = B.inc + s;
+    if (m <= 24) {
+        int2 ent[24];
+        int key[24];
+        for (int k = 0; k < m; ++k) {
+            int2 v = L[k];
+            int q = k;
+            int kv = B.id[v.y];
+            while (q > 0 && key[q - 1] > kv) { ent[q] = ent[q - 1]; key[q] = key[q - 1]; --q; }
+            ent[q] = v;
+            key[q] = kv;
+        }
+        for (int k = 0; k < m; ++k) L[k] = ent[k];
+    } else {
+        for (int k = 1; k < m; ++k) {
+            int2 v = L[k];
+            int kv = B.id[v.y];
+            int q = k;
+            while (q > 0 && B.id[L[q - 1].y] > kv) { L[q] = L[q - 1]; --q; }
+            L[q] = v;
+        }
+    }
+}
+
+static inline int nblk(int n, int t) { return n > 0 ? (n + t - 1) / t : 1; }
+
+int launch_cell_count(const SimParams& P, const DevBuf& B, cudaStream_t s) {
+    k_cell_count<<<nblk(P.n, BP_T), BP_T, 0, s>>>(P, B);
+    return 1;
+}
+int launch_cell_fill(const SimParams& P, const DevBuf& B, cudaStream_t s) {
+    k_cell_fill<<<nblk(P.n, BP_T), BP_T, 0, s>>>(P, B);
+    return 1;
+}
+int launch_pairs(const SimParams& P, const DevBuf& B, cudaStream_t s) {
+    k_pairs<<<nblk(P.n, BP_T), BP_T, 0, s>>>(P, B);
+    return 1;
+}
+int launch_contacts_build(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
+    k_contacts_build<<<nblk(P.n, BP_T), BP_T, 0, s>>>(P, B, parity);
+    return 1;
+}
+int launch_inc_sort(const SimParams& P, const DevBuf& B, cudaStream_t s) {
+    k_inc_sort<<<nblk(P.n, BP_T), BP_T, 0, s>>>(P, B);
+    return 1;
+}

@@ -1,0 +1,180 @@
+// Internal declarations of the GB300 DEM library: device data layout, launch
+// wrappers and small device helpers shared by the kernels.
+//
+// Data layout in HBM (slot = Morton-sorted particle index; stable id = index
+// in the caller's arrays):
+//   bodies   pos   double4_32a (x, y, z, r)        FP64 centres, exact contact tests
+//            posr  float4  (x, y, z, r)        FP32 copy for the broad phase
+//            vel0  float4  (v, 1/m)            velocity at the start of the step
+//            omg0  float4  (w, 1/I)
+//            velA/velB, omgA/omgB              Jacobi iterates v^k (ping-pong)
+//   contacts one record per sphere-sphere contact, owned by one body
+//            rec   3 x float4 per contact (normal, SPOOK row data, arms, cones)
+//            lamA  float4 (p_n, p_t1, p_t2, p_r.x), lamB float2 (p_r.y, p_r.z)
+//            lamW  2 x float4 world-frame impulses kept for the next warm start
+//   incidence per body, every contact it takes part in, ordered by the stable
+//            id of the other body: int2 (contact | side << 31, other slot)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dem.h"
+
+#define DEM_MAX_LEVELS 8
+#define DEM_MAX_GEOM 32
+#define DEM_MAX_OWN 32   // sphere-sphere contacts one body may own per step
+#define DEM_MAX_GEO 8    // sphere-geometry contacts per body per step
+#define DEM_FIX_SCALE 17592186044416.0  // 2^44: fixed-point scale of geometry impulses [N s]
+
+enum { DEM_FLAG_CAPACITY = 1, DEM_FLAG_NONFINITE = 2 };
+
+struct LevelGrid {
+    float ox, oy, oz;   // origin
+    float inv_cell;     // 1 / cell size
+    int nx, ny, nz;     // cells per axis (coordinates are clamped into range)
+    int offset;         // first global cell index of the level
+    float rmax;         // largest radius of the level
+    float cell;
+};
+
+struct GeomDev {
+    double c[3];
+    double R[9];        // row-major, column k = local axis k
+    double he[3];
+    double v[3];
+    double w[3];
+    int type;
+    float Estar;        // effective modulus of the sphere-geometry pair
+    float mu_t, mu_r;
+    float bound;        // radius of a sphere around c holding the primitive (box, cylinder)
+    float pad;
+};
+
+struct SimParams {
+    int n, ng, n_levels, n_it;
+    int max_contacts;   // capacity of the sphere-sphere contact arrays
+    int max_geo;        // capacity of the sphere-geometry contact arrays
+    int n_cells;
+    float dt, inv_dt;
+    float e_H, kn_scale, eps_reg, delta_floor;
+    float ups;          // SPOOK 1 / (1 + 4 tau/dt)
+    float Estar_ss;     // particle-particle effective modulus
+    float mu_t, mu_r;
+    float gx, gy, gz;
+    float tol;          // FP32 broad-phase tolerance [m], covers FP32 rounding of positions
+    LevelGrid lv[DEM_MAX_LEVELS];
+};
+
+// Device pointers of one bed.  The two warm-start generations (parity of the
+// step number) are indexed [0] / [1].
+struct DevBuf {
+    // bodies
+    double4_32a* pos;
+    float4* posr;
+    float4* vel0;
+    float4* omg0;
+    float4* vel[2];
+    float4* omg[2];
+    int* id;
+    int* lvl;
+    int* prev_of;       // old slot of each slot after a re-sort
+    int* resorted;      // 1 during the step that follows a re-sort
+    int* err;           // latched DEM_FLAG_* bits
+    // broad phase
+    int* body_cell;
+    int* cell_cnt;      // [n_cells + 1]
+    int* cell_start;    // [n_cells + 1]
+    int* cell_fill;     // [n_cells]
+    int* cell_body;     // [n]
+    // per-body candidate lists of the current step
+    int2* tmp_own;      // [n * DEM_MAX_OWN] (other slot, other stable id)
+    int* tmp_geo;       // [n * DEM_MAX_GEO] primitive index
+    int* own_cnt;       // [n + 1]
+    int* in_cnt;        // [n + 1]
+    int* geo_cnt;       // [n + 1]
+    int* in_fill;       // [n]
+    // scans
+    int* own_start[2];  // [n + 1] per parity
+    int* inc_start;     // [n + 1]
+    int* geo_start[2];  // [n + 1] per parity
+    // sphere-sphere contacts
+    int* c_other;       // [C] slot of body b
+    int* c_key[2];      // [C] stable id of body b, per parity
+    float4* rec;        // [3C]
+    float* c_delta;     // [C] overlap, kept for read-back
+    float4* lamA[2];    // [C] iterate ping-pong
+    float2* lamB[2];
+    float4* lamW[2];    // [2C] world-frame final impulses, per parity
+    int2* inc;          // [2C]
+    // sphere-geometry contacts (one-sided)
+    int* g_key[2];      // [max_geo] primitive index, per parity
+    float4* grec;       // [6 * max_geo]
+    float* g_delta;     // [max_geo]
+    float4* glamA[2];
+    float2* glamB[2];
+    float4* glamW[2];   // [2 * max_geo]
+    // kinematic geometry and its force accumulators
+    GeomDev* geom;      // [ng]
+    long long* gacc;    // [6 ng] fixed-point impulse and angular impulse
+    // re-sort scratch
+    unsigned* key_a; unsigned* key_b;
+    int* val_a; int* val_b;
+    int* hist;          // radix histogram [256 * blocks]
+    double4_32a* t_pos; float4* t_v; float4* t_w; int* t_id; int* t_lvl;
+    // scan scratch
+    int* scan_tmp;
+};
+
+// ----------------------------------------------------------------------------
+// launch wrappers (each returns the number of kernels it enqueued)
+// ----------------------------------------------------------------------------
+int launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s);
+// three exclusive scans at once; column b scans b + b2 element-wise
+int launch_scan3(const int* a, const int* b, const int* b2, const int* c, int* oa, int* ob, int* oc,
+                 int n, int* tmp, cudaStream_t s);
+int launch_cell_count(const SimParams& P, const DevBuf& B, cudaStream_t s);
+int launch_cell_fill(const SimParams& P, const DevBuf& B, cudaStream_t s);
+int launch_pairs(const SimParams& P, const DevBuf& B, cudaStream_t s);
+int launch_contacts_build(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
+int launch_inc_sort(const SimParams& P, const DevBuf& B, cudaStream_t s);
+int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
+int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
+int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s);
+int launch_integrate(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
+int launch_resort(const SimParams& P, const DevBuf& B, cudaStream_t s);
+int launch_radix_sort(unsigned* key_a, int* val_a, unsigned* key_b, int* val_b, int n, int* hist,
+                      int* tmp, cudaStream_t s);
+int radix_blocks(int n);
+
+// ----------------------------------------------------------------------------
+// device helpers
+// ----------------------------------------------------------------------------
+#define DEM_HD __host__ __device__ __forceinline__
+
+static __device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+static __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+static __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+static __device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+static __device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static __device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Orthonormal tangent basis (t1, t2) of a unit normal n with t2 = n x t1,
+// branch-free except for the sign of n.z: Duff et al., "Building an Orthonormal
+// Basis, Revisited", JCGT 6(1), 2017.
+static __device__ __forceinline__ void tangent_basis(float3 n, float3& t1, float3& t2) {
+    float sg = copysignf(1.0f, n.z);
+    float a = -1.0f / (sg + n.z);
+    float b = n.x * n.y * a;
+    t1 = make_float3(1.0f + sg * n.x * n.x * a, sg * b, -sg * n.x);
+    t2 = make_float3(b, sg + n.y * n.y * a, -n.y);
+}
+
+// cell coordinate of a position along one axis, clamped into the grid
+static __device__ __forceinline__ int cell_coord(float x, float o, float inv, int nmax) {
+    int c = __float2int_rd((x - o) * inv);
+    return c < 0 ? 0 : (c >= nmax ? nmax - 1 : c);
+}
+
+static __device__ __forceinline__ void set_flag(int* err, int bit) { atomicOr(err, bit); }

@@ -1,0 +1,425 @@
+// Contact rows, projected Jacobi sweeps and integration of one SPOOK step.
+//
+// Per contact (Sec. 2.2): normal n from b to a, overlap delta, Hertz mapping
+// g = -delta^{e_H}, eps_n = e_H / k_n with k_n = E* sqrt(d*) / 3.  The normal
+// row is written for the physical normal impulse p_n: the Hertz Jacobian
+// factor J = e_H max(delta, delta_floor)^{e_H - 1} is divided out, giving
+//   compliance  Sigma_n = 4 eps_n Y / (dt^2 J^2),  Y = 1 / (1 + 4 tau/dt)
+//   right side  b_n     = -(4/dt) Y g / J + Y n.(v_a - v_b) at the step start
+// (the SPOOK stepper, Lacoursiere 2007).  Tangential (2 rows) and rolling
+// (3 rows) rows have zero right side and compliance eps_reg Sigma_n.
+// Each Jacobi sweep updates every contact from the velocities of the previous
+// sweep: normal p_n <- max(0, p_n - D_n^{-1} w_n), tangential impulse projected
+// on the disc |p_t| <= mu_t p_n (Coulomb, Eq. 6), rolling impulse on the ball
+// |p_r| <= mu_r r_eff p_n (Eq. 7), where D are the diagonal blocks of
+// G M~^{-1} G^T + Sigma with masses split over each body's contacts (m / n_b).
+// The body pass sets v = v* + M^{-1} sum_c G_c^T p_c with v* = v + dt g.
+//
+// Execution: one thread per body.  A body walks its incidence list (ordered by
+// the other body's stable id), recomputes each contact's update from the two
+// bodies' previous iterates -- the same arithmetic on the same inputs at both
+// ends, so both ends agree bit for bit -- writes it if it owns the contact and
+// adds its own share of the impulse.  One kernel per sweep, no atomics.
+#include "dem_internal.cuh"
+#include "geometry.cuh"
+
+#define SV_T 128
+
+struct RowC {
+    float invDn, rhs, sig, invDt, invDr;
+};
+
+// SPOOK constants of one contact.  mlin = split 1/m_a + 1/m_b, mtan = the
+// angular part of the tangential diagonal, mrot = split 1/I_a + 1/I_b.
+static __device__ __forceinline__ RowC spook_row(const SimParams& P, float delta, float kn, float Gv,
+                                                 float mlin, float mtan, float mrot) {
+    RowC r;
+    const float eps_n = P.e_H / kn;
+    const float dfl = fmaxf(delta, P.delta_floor);
+    const float J = P.e_H * powf(dfl, P.e_H - 1.0f);
+    const float gap = -powf(delta, P.e_H);
+    const float sig_scaled = 4.0f * eps_n * P.ups * (P.inv_dt * P.inv_dt);
+    r.sig = sig_scaled / (J * J);
+    r.rhs = (-4.0f * P.inv_dt * P.ups * gap) / J + P.ups * Gv;
+    const float sig_t = P.eps_reg * r.sig;
+    r.invDn = 1.0f / (mlin + r.sig);
+    r.invDt = 1.0f / (mlin + mtan + sig_t);
+    r.invDr = 1.0f / (mrot + sig_t);
+    return r;
+}
+
+// world-frame warm start -> impulses in the basis of the new normal
+static __device__ __forceinline__ void warm_project(float4 w0, float4 w1, float3 n, float4& l0, float2& l1) {
+    float3 t1, t2;
+    tangent_basis(n, t1, t2);
+    const float3 pt = make_float3(w0.y, w0.z, w0.w);
+    l0 = make_float4(w0.x, dot(pt, t1), dot(pt, t2), w1.x);
+    l1 = make_float2(w1.y, w1.z);
+}
+
+// Impulse of a contact on the body at `side` (false = a, true = b) with arm
+// length l: linear  +-(p_n n + p_t),  angular  -l (n x p_t) +- p_r.
+static __device__ __forceinline__ void add_impulse(float3 n, float3 t1, float3 t2, float l, float pn,
+                                                   float pt1, float pt2, float3 pr, bool sideb,
+                                                   float3& accL, float3& accA) {
+    const float3 P = make_float3(pn * n.x + pt1 * t1.x + pt2 * t2.x, pn * n.y + pt1 * t1.y + pt2 * t2.y,
+                                 pn * n.z + pt1 * t1.z + pt2 * t2.z);
+    // n x p_t = pt1 t2 - pt2 t1
+    const float3 nxpt = make_float3(pt1 * t2.x - pt2 * t1.x, pt1 * t2.y - pt2 * t1.y, pt1 * t2.z - pt2 * t1.z);
+    if (!sideb) {
+        accL = accL + P;
+        accA = accA + (pr - l * nxpt);
+    } else {
+        accL = accL - P;
+        accA = accA - (pr + l * nxpt);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// contact rows + warm start
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n || *B.err) return;
+    const int q = p ^ 1;
+    const int prev = *B.resorted ? B.prev_of[i] : i;
+    const double4_32a xa = B.pos[i];
+    const float4 va = B.vel0[i], wa = B.omg0[i];
+    const int na = (B.inc_start[i + 1] - B.inc_start[i]) + (B.geo_start[p][i + 1] - B.geo_start[p][i]);
+    const float ra = (float)xa.w;
+
+    // sphere-sphere contacts owned by i (a = i)
+    const int os = B.own_start[p][i], oe = B.own_start[p][i + 1];
+    const int ps = B.own_start[q][prev], pe = B.own_start[q][prev + 1];
+    int kp = ps;
+    for (int c = os; c < oe; ++c) {
+        const int j = B.c_other[c];
+        const int key = B.c_key[p][c];
+        const double4_32a xb = B.pos[j];
+        const float4 vb = B.vel0[j], wb = B.omg0[j];
+        const int nb = (B.inc_start[j + 1] - B.inc_start[j]) + (B.geo_start[p][j + 1] - B.geo_start[p][j]);
+        // distance in double, overlap via (R^2 - d^2) / (R + d) to avoid cancellation
+        const double dx = __dsub_rn(xa.x, xb.x), dy = __dsub_rn(xa.y, xb.y), dz = __dsub_rn(xa.z, xb.z);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        const double R = __dadd_rn(xa.w, xb.w);
+        const float dist = sqrtf((float)d2);
+        const float delta = (float)__dsub_rn(__dmul_rn(R, R), d2) / ((float)R + dist);
+        const float inv = 1.0f / dist;
+        const float3 n = make_float3((float)dx * inv, (float)dy * inv, (float)dz * inv);
+        const float rb = (float)xb.w;
+        const float la = ra - 0.5f * delta, lb = rb - 0.5f * delta;
+        const float dstar = 2.0f * ra * rb / (ra + rb);   // (1/d_a + 1/d_b)^-1, also r_eff
+        const float kn = P.kn_scale * P.Estar_ss * sqrtf(dstar) / 3.0f;
+        const float ima = na * va.w, imb = nb * vb.w, iIa = na * wa.w, iIb = nb * wb.w;
+        const float Gv = dot(n, f3(va) - f3(vb));
+        const RowC rc = spook_row(P, delta, kn, Gv, ima + imb, la * la * iIa + lb * lb * iIb, iIa + iIb);
+        B.rec[3 * (size_t)c + 0] = make_float4(n.x, n.y, n.z, rc.invDn);
+        B.rec[3 * (size_t)c + 1] = make_float4(rc.rhs, rc.sig, rc.invDt, rc.invDr);
+        B.rec[3 * (size_t)c + 2] = make_float4(la, lb, P.mu_t, P.mu_r * dstar);
+        B.c_delta[c] = delta;
+        // warm start from the previous step's impulse of the same pair
+        while (kp < pe && B.c_key[q][kp] < key) ++kp;
+        float4 l0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 l1 = make_float2(0.f, 0.f);
+        if (kp < pe && B.c_key[q][kp] == key)
+            warm_project(B.lamW[q][2 * (size_t)kp], B.lamW[q][2 * (size_t)kp + 1], n, l0, l1);
+        B.lamA[0][c] = l0;
+        B.lamB[0][c] = l1;
+    }
+
+    // sphere-geometry contacts
+    const int gs = B.geo_start[p][i], ge = B.geo_start[p][i + 1];
+    const int gps = B.geo_start[q][prev], gpe = B.geo_start[q][prev + 1];
+    for (int k = gs; k < ge; ++k) {
+        const int g = B.g_key[p][k];
+        const GeomDev& G = B.geom[g];
+        // closest point, recomputed with the same routine the detection used
+        const GeoHit hh = geom_hit(G, xa.x, xa.y, xa.z, xa.w);
+        const double* qq = hh.q;
+        const float delta = (float)hh.delta;
+        const float3 n = make_float3((float)hh.n[0], (float)hh.n[1], (float)hh.n[2]);
+        const float la = ra - 0.5f * delta;
+        // contact point in the middle of the overlap, lever from the primitive's centre
+        const float3 lever = make_float3((float)(qq[0] - G.c[0]) + 0.5f * delta * n.x,
+                                         (float)(qq[1] - G.c[1]) + 0.5f * delta * n.y,
+                                         (float)(qq[2] - G.c[2]) + 0.5f * delta * n.z);
+        const float3 wg = make_float3((float)G.w[0], (float)G.w[1], (float)G.w[2]);
+        const float3 vgp = make_float3((float)G.v[0], (float)G.v[1], (float)G.v[2]) + cross(wg, lever);
+        const float dstar = 2.0f * ra;   // flat primitive: d_b -> infinity
+        const float kn = P.kn_scale * G.Estar * sqrtf(dstar) / 3.0f;
+        const float ima = na * va.w, iIa = na * wa.w;
+        const float Gv = dot(n, f3(va) - vgp);
+        const RowC rc = spook_row(P, delta, kn, Gv, ima, la * la * iIa, iIa);
+        float4* r = B.grec + 6 * (size_t)k;
+        r[0] = make_float4(n.x, n.y, n.z, rc.invDn);
+        r[1] = make_float4(rc.rhs, rc.sig, rc.invDt, rc.invDr);
+        r[2] = make_float4(la, G.mu_t, G.mu_r * ra, __int_as_float(g));
+        r[3] = make_float4(vgp.x, vgp.y, vgp.z, 0.f);
+        r[4] = make_float4(wg.x, wg.y, wg.z, 0.f);
+        r[5] = make_float4(lever.x, lever.y, lever.z, 0.f);
+        B.g_delta[k] = delta;
+        float4 l0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 l1 = make_float2(0.f, 0.f);
+        for (int kk = gps; kk < gpe; ++kk)
+            if (B.g_key[q][kk] == g) {
+                warm_project(B.glamW[q][2 * (size_t)kk], B.glamW[q][2 * (size_t)kk + 1], n, l0, l1);
+                break;
+            }
+        B.glamA[0][k] = l0;
+        B.glamB[0][k] = l1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the canonical contact update, identical at both ends of a contact
+// ---------------------------------------------------------------------------
+struct Upd {
+    float pn, pt1, pt2;
+    float3 pr, t1, t2;
+};
+
+static __device__ __forceinline__ Upd contact_update(float4 r0, float4 r1, float la, float lb, float mu_t,
+                                                     float mur, float4 l0, float2 l1, float3 dv,
+                                                     float3 wa, float3 wb, float eps_reg) {
+    Upd u;
+    const float3 n = f3(r0);
+    const float sig = r1.y, sig_t = eps_reg * r1.y;
+    // normal: 0 <= p_n complementary to the SPOOK row (Eq. 5)
+    const float wn = dot(n, dv) + sig * l0.x - r1.x;
+    u.pn = fmaxf(0.0f, l0.x - r0.w * wn);
+    // contact-point relative velocity: dv + w_a x (-l_a n) - w_b x (l_b n)
+    const float3 uc = dv - cross(la * wa + lb * wb, n);
+    tangent_basis(n, u.t1, u.t2);
+    float pt1 = l0.y - r1.z * (dot(uc, u.t1) + sig_t * l0.y);
+    float pt2 = l0.z - r1.z * (dot(uc, u.t2) + sig_t * l0.z);
+    const float bt = mu_t * u.pn;
+    const float m2 = pt1 * pt1 + pt2 * pt2;
+    if (m2 > bt * bt) {   // Coulomb disc (Eq. 6)
+        const float s = bt / sqrtf(m2);
+        pt1 *= s;
+        pt2 *= s;
+    }
+    u.pt1 = pt1;
+    u.pt2 = pt2;
+    // rolling and twisting: ball |p_r| <= mu_r r_eff p_n (Eq. 7)
+    const float3 pr0 = make_float3(l0.w, l1.x, l1.y);
+    float3 pr = pr0 - r1.w * ((wa - wb) + sig_t * pr0);
+    const float br = mur * u.pn;
+    const float q2 = dot(pr, pr);
+    if (q2 > br * br) pr = (br / sqrtf(q2)) * pr;
+    u.pr = pr;
+    return u;
+}
+
+static __device__ __forceinline__ void write_world(float4* W, size_t c, float3 n, const Upd& u) {
+    const float3 pt = u.pt1 * u.t1 + u.pt2 * u.t2;
+    W[2 * c] = make_float4(u.pn, pt.x, pt.y, pt.z);
+    W[2 * c + 1] = make_float4(u.pr.x, u.pr.y, u.pr.z, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// v^0 = v* + M^-1 sum G^T p^0  (warm-start impulses)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SV_T) k_v0(SimParams P, DevBuf B, int p, int write_final) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n || *B.err) return;
+    float3 accL = make_float3(0.f, 0.f, 0.f), accA = make_float3(0.f, 0.f, 0.f);
+    for (int e = B.inc_start[i]; e < B.inc_start[i + 1]; ++e) {
+        const int2 ent = B.inc[e];
+        const bool sideb = ent.x < 0;
+        const int c = ent.x & 0x7fffffff;
+        const float4 r0 = B.rec[3 * (size_t)c], r2 = B.rec[3 * (size_t)c + 2];
+        const float4 l0 = B.lamA[0][c];
+        const float2 l1 = B.lamB[0][c];
+        const float3 n = f3(r0);
+        float3 t1, t2;
+        tangent_basis(n, t1, t2);
+        add_impulse(n, t1, t2, sideb ? r2.y : r2.x, l0.x, l0.y, l0.z, make_float3(l0.w, l1.x, l1.y),
+                    sideb, accL, accA);
+        if (write_final && !sideb) {
+            Upd u;
+            u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
+            u.t1 = t1; u.t2 = t2;
+            write_world(B.lamW[p], c, n, u);
+        }
+    }
+    for (int k = B.geo_start[p][i]; k < B.geo_start[p][i + 1]; ++k) {
+        const float4* r = B.grec + 6 * (size_t)k;
+        const float4 r0 = r[0], r2 = r[2];
+        const float4 l0 = B.glamA[0][k];
+        const float2 l1 = B.glamB[0][k];
+        const float3 n = f3(r0);
+        float3 t1, t2;
+        tangent_basis(n, t1, t2);
+        add_impulse(n, t1, t2, r2.x, l0.x, l0.y, l0.z, make_float3(l0.w, l1.x, l1.y), false, accL, accA);
+        if (write_final) {
+            Upd u;
+            u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
+            u.t1 = t1; u.t2 = t2;
+            write_world(B.glamW[p], k, n, u);
+        }
+    }
+    const float4 v0 = B.vel0[i], w0 = B.omg0[i];
+    const float gm = v0.w > 0.0f ? P.dt : 0.0f;
+    const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
+    const float3 v = vs + v0.w * accL;
+    const float3 w = f3(w0) + w0.w * accA;
+    B.vel[0][i] = make_float4(v.x, v.y, v.z, v0.w);
+    B.omg[0][i] = make_float4(w.x, w.y, w.z, w0.w);
+}
+
+// ---------------------------------------------------------------------------
+// one projected Jacobi sweep
+// ---------------------------------------------------------------------------
+template <bool LAST>
+__global__ void __launch_bounds__(SV_T) k_jacobi(SimParams P, DevBuf B, int p, int src) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n || *B.err) return;
+    const int dst = src ^ 1;
+    const float4* __restrict__ vin = B.vel[src];
+    const float4* __restrict__ win = B.omg[src];
+    const float4* __restrict__ lAin = B.lamA[src];
+    const float2* __restrict__ lBin = B.lamB[src];
+    float4* lAout = B.lamA[dst];
+    float2* lBout = B.lamB[dst];
+    const float4 vi4 = vin[i], wi4 = win[i];
+    const float3 vi = f3(vi4), wi = f3(wi4);
+    float3 accL = make_float3(0.f, 0.f, 0.f), accA = make_float3(0.f, 0.f, 0.f);
+    const int e1 = B.inc_start[i + 1];
+    for (int e = B.inc_start[i]; e < e1; ++e) {
+        const int2 ent = B.inc[e];
+        const bool sideb = ent.x < 0;
+        const int c = ent.x & 0x7fffffff;
+        const int j = ent.y;
+        const float4 r0 = B.rec[3 * (size_t)c], r1 = B.rec[3 * (size_t)c + 1], r2 = B.rec[3 * (size_t)c + 2];
+        const float4 l0 = lAin[c];
+        const float2 l1 = lBin[c];
+        const float3 vj = f3(vin[j]), wj = f3(win[j]);
+        const float3 dv = sideb ? vj - vi : vi - vj;
+        const float3 wa = sideb ? wj : wi, wb = sideb ? wi : wj;
+        const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, dv, wa, wb, P.eps_reg);
+        if (!sideb) {
+            if (LAST) {
+                write_world(B.lamW[p], c, f3(r0), u);
+            } else {
+                lAout[c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+                lBout[c] = make_float2(u.pr.y, u.pr.z);
+            }
+        }
+        add_impulse(f3(r0), u.t1, u.t2, sideb ? r2.y : r2.x, u.pn, u.pt1, u.pt2, u.pr, sideb, accL, accA);
+    }
+    const int g1 = B.geo_start[p][i + 1];
+    for (int k = B.geo_start[p][i]; k < g1; ++k) {
+        const float4* r = B.grec + 6 * (size_t)k;
+        const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+        const float4 l0 = B.glamA[src][k];
+        const float2 l1 = B.glamB[src][k];
+        const float3 dv = vi - f3(r3);
+        const Upd u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, dv, wi, f3(r4), P.eps_reg);
+        if (LAST) {
+            write_world(B.glamW[p], k, f3(r0), u);
+        } else {
+            B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+            B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
+        }
+        add_impulse(f3(r0), u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
+    }
+    const float4 v0 = B.vel0[i], w0 = B.omg0[i];
+    const float gm = v0.w > 0.0f ? P.dt : 0.0f;
+    const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
+    const float3 v = vs + v0.w * accL;
+    const float3 w = f3(w0) + w0.w * accA;
+    B.vel[dst][i] = make_float4(v.x, v.y, v.z, v0.w);
+    B.omg[dst][i] = make_float4(w.x, w.y, w.z, w0.w);
+}
+
+// ---------------------------------------------------------------------------
+// x += dt v (SPOOK position update), geometry forces, kinematic geometry
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p, int src) {
+    __shared__ long long sacc[6 * DEM_MAX_GEOM];
+    for (int t = threadIdx.x; t < 6 * P.ng; t += blockDim.x) sacc[t] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = !*B.err;
+    if (i < P.n && ok) {
+        const float4 v = B.vel[src][i], w = B.omg[src][i];
+        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(w.x) && isfinite(w.y) &&
+              isfinite(w.z)))
+            set_flag(B.err, DEM_FLAG_NONFINITE);
+        B.vel0[i] = v;
+        B.omg0[i] = w;
+        double4_32a x = B.pos[i];
+        const double h = (double)P.dt;
+        x.x = __dadd_rn(x.x, __dmul_rn(h, (double)v.x));
+        x.y = __dadd_rn(x.y, __dmul_rn(h, (double)v.y));
+        x.z = __dadd_rn(x.z, __dmul_rn(h, (double)v.z));
+        B.pos[i] = x;
+        B.posr[i] = make_float4((float)x.x, (float)x.y, (float)x.z, (float)x.w);
+        for (int k = B.geo_start[p][i]; k < B.geo_start[p][i + 1]; ++k) {
+            const float4* r = B.grec + 6 * (size_t)k;
+            const float4 r0 = r[0], r2 = r[2], r5 = r[5];
+            const float4 W0 = B.glamW[p][2 * (size_t)k], W1 = B.glamW[p][2 * (size_t)k + 1];
+            const int g = __float_as_int(r2.w);
+            // impulse of the particle on the primitive: -(p_n n + p_t) at the lever, -p_r
+            const float3 Pg = make_float3(-(W0.x * r0.x + W0.y), -(W0.x * r0.y + W0.z), -(W0.x * r0.z + W0.w));
+            const float3 Tg = cross(f3(r5), Pg) - make_float3(W1.x, W1.y, W1.z);
+            const float vals[6] = {Pg.x, Pg.y, Pg.z, Tg.x, Tg.y, Tg.z};
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+                atomicAdd((unsigned long long*)&sacc[6 * g + c],
+                          (unsigned long long)__double2ll_rn((double)vals[c] * DEM_FIX_SCALE));
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 6 * P.ng; t += blockDim.x)
+        if (sacc[t] != 0) atomicAdd((unsigned long long*)&B.gacc[t], (unsigned long long)sacc[t]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // kinematic primitives: translate with v, rotate with w (Rodrigues)
+        const double h = (double)P.dt;
+        for (int g = 0; g < P.ng; ++g) {
+            GeomDev& G = B.geom[g];
+            for (int c = 0; c < 3; ++c) G.c[c] = __dadd_rn(G.c[c], __dmul_rn(h, G.v[c]));
+            const double wn = sqrt(G.w[0] * G.w[0] + G.w[1] * G.w[1] + G.w[2] * G.w[2]);
+            if (wn > 0.0) {
+                const double ax[3] = {G.w[0] / wn, G.w[1] / wn, G.w[2] / wn};
+                const double th = wn * h, cs = cos(th), sn = sin(th);
+                double Rot[3][3];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) Rot[a][b] = (a == b ? cs : 0.0) + (1.0 - cs) * ax[a] * ax[b];
+                Rot[0][1] -= sn * ax[2]; Rot[0][2] += sn * ax[1];
+                Rot[1][0] += sn * ax[2]; Rot[1][2] -= sn * ax[0];
+                Rot[2][0] -= sn * ax[1]; Rot[2][1] += sn * ax[0];
+                double Rn[9];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        Rn[3 * a + b] = Rot[a][0] * G.R[b] + Rot[a][1] * G.R[3 + b] + Rot[a][2] * G.R[6 + b];
+                for (int k = 0; k < 9; ++k) G.R[k] = Rn[k];
+            }
+        }
+        *B.resorted = 0;
+    }
+}
+
+static inline int nblk(int n, int t) { return n > 0 ? (n + t - 1) / t : 1; }
+
+int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
+    k_setup<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity);
+    return 1;
+}
+int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
+    k_v0<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity, P.n_it == 0 ? 1 : 0);
+    return 1;
+}
+int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s) {
+    const int src = it & 1;
+    if (it == P.n_it - 1)
+        k_jacobi<true><<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity, src);
+    else
+        k_jacobi<false><<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity, src);
+    return 1;
+}
+int launch_integrate(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
+    k_integrate<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity, P.n_it & 1);
+    return 1;
+}

@@ -1,0 +1,136 @@
+"""GPU-only properties: determinism, invariance under the Morton re-sort
+period, edge cases and error reporting through the C ABI."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from dem_cases import box_geoms, compressed_cloud, make_gpu, params
+from paper_2501_05300_gb300 import beds, dem
+
+pytestmark = pytest.mark.gpu
+
+
+def run(resort_every, steps=40, n=2000, seed=11):
+    x, r = compressed_cloud(n, seed=seed)
+    lo, hi = x.min(0) - 0.004, x.max(0) + 0.004
+    g = make_gpu(x, r, params(n_it=30), box_geoms(lo, hi), resort_every=resort_every)
+    g.step(steps)
+    out = g.read_state(), g.read_forces(0)
+    g.close()
+    return out
+
+
+def test_bitwise_deterministic():
+    (x1, v1, w1), f1 = run(10)
+    (x2, v2, w2), f2 = run(10)
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2) and np.array_equal(w1, w2)
+    assert np.array_equal(f1[0], f2[0])
+
+
+def test_results_do_not_depend_on_the_resort_period():
+    """Sums run in stable-id order and the warm start is keyed by stable ids,
+    so re-sorting every step or once gives bit-identical trajectories."""
+    (x1, v1, w1), f1 = run(1)
+    (x2, v2, w2), f2 = run(1000)
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2) and np.array_equal(w1, w2)
+    assert np.array_equal(f1[0], f2[0])
+
+
+def test_empty_bed():
+    g = make_gpu(np.zeros((0, 3)), np.zeros(0, np.float32), params(), box_geoms((0, 0, 0), (1, 1, 1)))
+    g.step(3)
+    x, v, w = g.read_state()
+    assert x.shape == (0, 3)
+    assert g.read_contacts()[0].shape == (0,)
+    f, t, s = g.read_forces(0)
+    assert np.all(f == 0)
+    g.close()
+
+
+def test_single_falling_sphere_matches_free_fall():
+    p = params(n_it=10)
+    g = make_gpu(np.array([[0.0, 0.0, 1.0]]), np.array([0.005], np.float32), p)
+    g.step(100)
+    x, v, w = g.read_state()
+    # symplectic Euler: v = g t, z = z0 + g dt^2 k(k+1)/2 (velocity kept in FP32)
+    assert v[0, 2] == pytest.approx(-9.81 * 100 * 1e-5, rel=1e-5)
+    assert x[0, 2] == pytest.approx(1.0 - 9.81 * 1e-10 * 100 * 101 / 2, abs=1e-10)
+    g.close()
+
+
+def test_no_iterations_is_allowed():
+    x, r = compressed_cloud(300, seed=3)
+    g = make_gpu(x, r, params(n_it=0))
+    g.step(2)
+    a, b, lam, dl = g.read_contacts()
+    assert len(a) > 0 and np.all(lam == 0)      # no warm start on the first steps
+    g.close()
+
+
+def test_capacity_overflow_is_reported_and_latched():
+    x, r = compressed_cloud(2000, seed=4)
+    g = make_gpu(x, r, params(n_it=5), contact_capacity=100)
+    g.step(1)
+    with pytest.raises(dem.DemError) as e:
+        g.sync()
+    assert e.value.status == dem.DEM_ERR_CAPACITY
+    with pytest.raises(dem.DemError) as e:
+        g.step(1)
+    assert e.value.status == dem.DEM_ERR_STATE
+    g.close()
+
+
+def test_invalid_arguments_are_rejected():
+    x, r = compressed_cloud(10, seed=1)
+    with pytest.raises(dem.DemError) as e:
+        make_gpu(x, -r, params())
+    assert e.value.status == dem.DEM_ERR_ARG
+    with pytest.raises(dem.DemError):
+        make_gpu(x, r, params(dt=0.0))
+    g = make_gpu(x, r, params(), box_geoms((0, 0, 0), (1, 1, 1)))
+    with pytest.raises(dem.DemError):
+        g.apply_plate_velocity(99, (0, 0, 1))
+    with pytest.raises(dem.DemError):
+        g.read_forces(-1)
+    with pytest.raises(dem.DemError):
+        g.step(-1)
+    g.close()
+
+
+def test_particles_leaving_the_grid_still_collide():
+    """Two spheres race far outside the grids laid over the initial bounding box
+    and catch up with each other there: clamped cell coordinates keep the
+    broad phase exact."""
+    x = np.array([[0.0, 0.0, 0.0], [0.0095, 0.0, 0.0], [0.1, 0.2, 0.0], [0.112, 0.2, 0.0]])
+    r = np.full(4, 0.005, np.float32)
+    v = np.array([[0, 0, 0], [0, 0, 0], [1000.0, 0, 0], [999.5, 0, 0]], np.float32)
+    g = make_gpu(x, r, params(gravity=(0.0, 0.0, 0.0), dt=1e-3, n_it=5), v=v)
+    met = False
+    for k in range(10):
+        g.step(1)
+        a, b, lam, dl = g.read_contacts()
+        pairs = {tuple(sorted(p)) for p in zip(a.tolist(), b.tolist())}
+        if k == 0:
+            assert pairs == {(0, 1)}
+        if (2, 3) in pairs:
+            met = True
+            break
+    assert met
+    xs = g.read_state()[0]
+    assert xs[2, 0] > 3.0                      # far outside the initial grids
+    g.close()
+
+
+def test_torch_device_buffers_are_accepted():
+    import torch
+    x, r = compressed_cloud(500, seed=9)
+    xt = torch.tensor(x, device="cuda")
+    rt = torch.tensor(r, device="cuda")
+    g1 = make_gpu(xt, rt, params(n_it=20))
+    g2 = make_gpu(x, r, params(n_it=20))
+    g1.step(3)
+    g2.step(3)
+    assert np.array_equal(g1.read_state()[1], g2.read_state()[1])
+    g1.close()
+    g2.close()

@@ -118,7 +118,7 @@ class ClockSampler:
 def settle_and_place(torch, dem, spec, settle_steps):
     """Settle the lattice (generation friction mu_t 0.1, mu_r 0.01, Sec. 3.1)
     at dt = 2e-4 (Eq. 9 allows ~2.7e-4 for d = 5 mm under the bed's own
-    weight), then put the plate 0.5 mm above the surface under it."""
+    weight), then put the plate 0.1 mm above the surface under it."""
     plate = spec.plate
     geoms = [g for g in spec.geoms]
     hold = beds.GeomSpec(**{**spec.geoms[plate].__dict__})
@@ -133,7 +133,7 @@ def settle_and_place(torch, dem, spec, settle_steps):
     under = (x[:, 0] - pc.c[0]) ** 2 + (x[:, 1] - pc.c[1]) ** 2 <= pc.he[0] ** 2
     top = float((x[under, 2] + spec.r[under]).max()) if under.any() else float((x[:, 2] + spec.r).max())
     placed = beds.GeomSpec(**{**pc.__dict__})
-    placed.c = (pc.c[0], pc.c[1], top + 0.0005 + pc.he[2])
+    placed.c = (pc.c[0], pc.c[1], top + 0.0001 + pc.he[2])
     geoms = list(spec.geoms)
     geoms[plate] = placed
     return x, v, w, geoms
@@ -149,11 +149,11 @@ def run_gpu(args, rank, world):
     x, v, w, geoms = settle_and_place(torch, dem, spec, args.settle)
     m = spec.material
     bed = dem.Bed(x, spec.r, v=v, w=w, geoms=geoms, rho=m.rho, mu_t=m.mu_t, mu_r=m.mu_r,
-                  n_it=N_IT, dt=DT)
+                  n_it=N_IT, dt=DT, lanes=args.lanes)
     pl = spec.plate
-    # approach: bring the plate into contact (untimed), then 0.01 m/s
+    # approach: bring the plate 0.2 mm into the surface (untimed), then 0.01 m/s
     bed.apply_plate_velocity(pl, (0.0, 0.0, -0.05))
-    bed.step(200)
+    bed.step(600)
     bed.apply_plate_velocity(pl, (0.0, 0.0, -PLATE_V))
     bed.step(args.warmup)
     bed.sync()
@@ -256,6 +256,7 @@ def main():
     ap.add_argument("--settle", type=int, default=2000)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, help="threads per particle in the sweep (0: library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

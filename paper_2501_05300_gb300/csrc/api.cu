@@ -249,6 +249,11 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     if (cap > (int64_t)0x3fffffff) cap = 0x3fffffff;
     P.max_contacts = (int)cap;
     P.max_geo = 2 * n + 1024;
+    P.lanes = d->lanes > 0 ? d->lanes : 4;
+    if (P.lanes != 1 && P.lanes != 2 && P.lanes != 4 && P.lanes != 8) {
+        release(b);
+        return fail(DEM_ERR_ARG, "lanes = %d is not 1, 2, 4 or 8", d->lanes);
+    }
 
     // grids over the particle bounding box plus a margin
     double ext = 0.0, absmax = 0.0;

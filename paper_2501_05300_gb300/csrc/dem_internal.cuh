@@ -62,6 +62,7 @@ struct SimParams {
     float mu_t, mu_r;
     float gx, gy, gz;
     float tol;          // FP32 broad-phase tolerance [m], covers FP32 rounding of positions
+    int lanes;          // threads per body in the Jacobi sweep (1, 2, 4 or 8)
     LevelGrid lv[DEM_MAX_LEVELS];
 };
 

@@ -218,119 +218,106 @@ static __device__ __forceinline__ void write_world(float4* W, size_t c, float3 n
 }
 
 // ---------------------------------------------------------------------------
-// v^0 = v* + M^-1 sum G^T p^0  (warm-start impulses)
+// Body pass (UPDATE = false: v^0 from the warm-start impulses) and projected
+// Jacobi sweep (UPDATE = true).  T lanes share one body: lane l takes the
+// body's incidence entries l, l+T, l+2T, ... and the lanes' impulse sums are
+// combined by a fixed butterfly of shuffles, so the result is deterministic.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SV_T) k_v0(SimParams P, DevBuf B, int p, int write_final) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n || *B.err) return;
-    float3 accL = make_float3(0.f, 0.f, 0.f), accA = make_float3(0.f, 0.f, 0.f);
-    for (int e = B.inc_start[i]; e < B.inc_start[i + 1]; ++e) {
-        const int2 ent = B.inc[e];
-        const bool sideb = ent.x < 0;
-        const int c = ent.x & 0x7fffffff;
-        const float4 r0 = B.rec[3 * (size_t)c], r2 = B.rec[3 * (size_t)c + 2];
-        const float4 l0 = B.lamA[0][c];
-        const float2 l1 = B.lamB[0][c];
-        const float3 n = f3(r0);
-        float3 t1, t2;
-        tangent_basis(n, t1, t2);
-        add_impulse(n, t1, t2, sideb ? r2.y : r2.x, l0.x, l0.y, l0.z, make_float3(l0.w, l1.x, l1.y),
-                    sideb, accL, accA);
-        if (write_final && !sideb) {
-            Upd u;
-            u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
-            u.t1 = t1; u.t2 = t2;
-            write_world(B.lamW[p], c, n, u);
-        }
-    }
-    for (int k = B.geo_start[p][i]; k < B.geo_start[p][i + 1]; ++k) {
-        const float4* r = B.grec + 6 * (size_t)k;
-        const float4 r0 = r[0], r2 = r[2];
-        const float4 l0 = B.glamA[0][k];
-        const float2 l1 = B.glamB[0][k];
-        const float3 n = f3(r0);
-        float3 t1, t2;
-        tangent_basis(n, t1, t2);
-        add_impulse(n, t1, t2, r2.x, l0.x, l0.y, l0.z, make_float3(l0.w, l1.x, l1.y), false, accL, accA);
-        if (write_final) {
-            Upd u;
-            u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
-            u.t1 = t1; u.t2 = t2;
-            write_world(B.glamW[p], k, n, u);
-        }
-    }
-    const float4 v0 = B.vel0[i], w0 = B.omg0[i];
-    const float gm = v0.w > 0.0f ? P.dt : 0.0f;
-    const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
-    const float3 v = vs + v0.w * accL;
-    const float3 w = f3(w0) + w0.w * accA;
-    B.vel[0][i] = make_float4(v.x, v.y, v.z, v0.w);
-    B.omg[0][i] = make_float4(w.x, w.y, w.z, w0.w);
+template <int T>
+static __device__ __forceinline__ float sub_sum(float v) {
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// ---------------------------------------------------------------------------
-// one projected Jacobi sweep
-// ---------------------------------------------------------------------------
-template <bool LAST>
-__global__ void __launch_bounds__(SV_T) k_jacobi(SimParams P, DevBuf B, int p, int src) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n || *B.err) return;
+template <int T, bool UPDATE, bool LAST>
+__global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, int src, int write_final) {
+    if (*B.err) return;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / T, lane = gt % T;
+    const bool active = i < P.n;
     const int dst = src ^ 1;
-    const float4* __restrict__ vin = B.vel[src];
-    const float4* __restrict__ win = B.omg[src];
+    const float4* __restrict__ vin = UPDATE ? B.vel[src] : B.vel0;
+    const float4* __restrict__ win = UPDATE ? B.omg[src] : B.omg0;
     const float4* __restrict__ lAin = B.lamA[src];
     const float2* __restrict__ lBin = B.lamB[src];
-    float4* lAout = B.lamA[dst];
-    float2* lBout = B.lamB[dst];
-    const float4 vi4 = vin[i], wi4 = win[i];
-    const float3 vi = f3(vi4), wi = f3(wi4);
     float3 accL = make_float3(0.f, 0.f, 0.f), accA = make_float3(0.f, 0.f, 0.f);
-    const int e1 = B.inc_start[i + 1];
-    for (int e = B.inc_start[i]; e < e1; ++e) {
-        const int2 ent = B.inc[e];
-        const bool sideb = ent.x < 0;
-        const int c = ent.x & 0x7fffffff;
-        const int j = ent.y;
-        const float4 r0 = B.rec[3 * (size_t)c], r1 = B.rec[3 * (size_t)c + 1], r2 = B.rec[3 * (size_t)c + 2];
-        const float4 l0 = lAin[c];
-        const float2 l1 = lBin[c];
-        const float3 vj = f3(vin[j]), wj = f3(win[j]);
-        const float3 dv = sideb ? vj - vi : vi - vj;
-        const float3 wa = sideb ? wj : wi, wb = sideb ? wi : wj;
-        const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, dv, wa, wb, P.eps_reg);
-        if (!sideb) {
-            if (LAST) {
-                write_world(B.lamW[p], c, f3(r0), u);
+    float4 vi4 = make_float4(0.f, 0.f, 0.f, 0.f), wi4 = vi4;
+    if (active) {
+        vi4 = vin[i];
+        wi4 = win[i];
+        const float3 vi = f3(vi4), wi = f3(wi4);
+        const int e1 = B.inc_start[i + 1];
+        for (int e = B.inc_start[i] + lane; e < e1; e += T) {
+            const int2 ent = B.inc[e];
+            const bool sideb = ent.x < 0;
+            const int c = ent.x & 0x7fffffff;
+            const float4 r0 = B.rec[3 * (size_t)c], r2 = B.rec[3 * (size_t)c + 2];
+            const float4 l0 = lAin[c];
+            const float2 l1 = lBin[c];
+            const float3 n = f3(r0);
+            if (UPDATE) {
+                const int j = ent.y;
+                const float4 r1 = B.rec[3 * (size_t)c + 1];
+                const float3 vj = f3(vin[j]), wj = f3(win[j]);
+                const float3 dv = sideb ? vj - vi : vi - vj;
+                const float3 wa = sideb ? wj : wi, wb = sideb ? wi : wj;
+                const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, dv, wa, wb, P.eps_reg);
+                if (!sideb) {
+                    if (LAST) {
+                        write_world(B.lamW[p], c, n, u);
+                    } else {
+                        B.lamA[dst][c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+                        B.lamB[dst][c] = make_float2(u.pr.y, u.pr.z);
+                    }
+                }
+                add_impulse(n, u.t1, u.t2, sideb ? r2.y : r2.x, u.pn, u.pt1, u.pt2, u.pr, sideb, accL, accA);
             } else {
-                lAout[c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
-                lBout[c] = make_float2(u.pr.y, u.pr.z);
+                Upd u;
+                tangent_basis(n, u.t1, u.t2);
+                u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
+                if (write_final && !sideb) write_world(B.lamW[p], c, n, u);
+                add_impulse(n, u.t1, u.t2, sideb ? r2.y : r2.x, u.pn, u.pt1, u.pt2, u.pr, sideb, accL, accA);
             }
         }
-        add_impulse(f3(r0), u.t1, u.t2, sideb ? r2.y : r2.x, u.pn, u.pt1, u.pt2, u.pr, sideb, accL, accA);
-    }
-    const int g1 = B.geo_start[p][i + 1];
-    for (int k = B.geo_start[p][i]; k < g1; ++k) {
-        const float4* r = B.grec + 6 * (size_t)k;
-        const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
-        const float4 l0 = B.glamA[src][k];
-        const float2 l1 = B.glamB[src][k];
-        const float3 dv = vi - f3(r3);
-        const Upd u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, dv, wi, f3(r4), P.eps_reg);
-        if (LAST) {
-            write_world(B.glamW[p], k, f3(r0), u);
-        } else {
-            B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
-            B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
+        const int g1 = B.geo_start[p][i + 1];
+        for (int k = B.geo_start[p][i] + lane; k < g1; k += T) {
+            const float4* r = B.grec + 6 * (size_t)k;
+            const float4 r0 = r[0], r2 = r[2];
+            const float4 l0 = B.glamA[src][k];
+            const float2 l1 = B.glamB[src][k];
+            const float3 n = f3(r0);
+            Upd u;
+            if (UPDATE) {
+                const float4 r1 = r[1], r3 = r[3], r4 = r[4];
+                u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4), P.eps_reg);
+                if (LAST) {
+                    write_world(B.glamW[p], k, n, u);
+                } else {
+                    B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+                    B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
+                }
+            } else {
+                tangent_basis(n, u.t1, u.t2);
+                u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
+                if (write_final) write_world(B.glamW[p], k, n, u);
+            }
+            add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
         }
-        add_impulse(f3(r0), u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
     }
+    if (T > 1) {
+        accL = make_float3(sub_sum<T>(accL.x), sub_sum<T>(accL.y), sub_sum<T>(accL.z));
+        accA = make_float3(sub_sum<T>(accA.x), sub_sum<T>(accA.y), sub_sum<T>(accA.z));
+    }
+    if (!active || lane != 0) return;
     const float4 v0 = B.vel0[i], w0 = B.omg0[i];
     const float gm = v0.w > 0.0f ? P.dt : 0.0f;
     const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
     const float3 v = vs + v0.w * accL;
     const float3 w = f3(w0) + w0.w * accA;
-    B.vel[dst][i] = make_float4(v.x, v.y, v.z, v0.w);
-    B.omg[dst][i] = make_float4(w.x, w.y, w.z, w0.w);
+    const int out = UPDATE ? dst : 0;
+    B.vel[out][i] = make_float4(v.x, v.y, v.z, v0.w);
+    B.omg[out][i] = make_float4(w.x, w.y, w.z, w0.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -407,16 +394,32 @@ int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s
     k_setup<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity);
     return 1;
 }
+template <int T>
+static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int src, bool update, bool last,
+                         int write_final, cudaStream_t s) {
+    const int blocks = nblk(P.n * T, SV_T);
+    if (!update) k_sweep<T, false, false><<<blocks, SV_T, 0, s>>>(P, B, parity, 0, write_final);
+    else if (last) k_sweep<T, true, true><<<blocks, SV_T, 0, s>>>(P, B, parity, src, 0);
+    else k_sweep<T, true, false><<<blocks, SV_T, 0, s>>>(P, B, parity, src, 0);
+}
+
+static void sweep_dispatch(const SimParams& P, const DevBuf& B, int parity, int src, bool update, bool last,
+                           int write_final, cudaStream_t s) {
+    switch (P.lanes) {
+        case 1: sweep_launch<1>(P, B, parity, src, update, last, write_final, s); break;
+        case 2: sweep_launch<2>(P, B, parity, src, update, last, write_final, s); break;
+        case 8: sweep_launch<8>(P, B, parity, src, update, last, write_final, s); break;
+        default: sweep_launch<4>(P, B, parity, src, update, last, write_final, s); break;
+    }
+}
+
 int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
-    k_v0<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity, P.n_it == 0 ? 1 : 0);
+    // v^0 goes to vel[0]; with no sweeps the warm start is also the final impulse
+    sweep_dispatch(P, B, parity, 0, false, false, P.n_it == 0 ? 1 : 0, s);
     return 1;
 }
 int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s) {
-    const int src = it & 1;
-    if (it == P.n_it - 1)
-        k_jacobi<true><<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity, src);
-    else
-        k_jacobi<false><<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity, src);
+    sweep_dispatch(P, B, parity, it & 1, true, it == P.n_it - 1, 0, s);
     return 1;
 }
 int launch_integrate(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {

@@ -53,7 +53,8 @@ class dem_bed_desc(C.Structure):
                 ("n_it", C.c_int32), ("gravity", C.c_float * 3), ("kn_scale", C.c_float),
                 ("eps_reg", C.c_float), ("delta_floor", C.c_float), ("n_geom", C.c_int32),
                 ("geom", C.POINTER(dem_geom)), ("contact_capacity", C.c_int64),
-                ("resort_every", C.c_int32), ("level_ratio", C.c_float), ("alloc", ALLOC_FN),
+                ("resort_every", C.c_int32), ("level_ratio", C.c_float), ("lanes", C.c_int32),
+                ("alloc", ALLOC_FN),
                 ("free_fn", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -184,7 +185,8 @@ class Bed:
     def __init__(self, x, r, *, v=None, w=None, geoms=(), rho=2600.0, E=1e9, nu=0.15, mu_t=0.5,
                  mu_r=0.02, e_H=1.25, damp_steps=4.5, dt=1e-5, n_it=100, gravity=(0.0, 0.0, -9.81),
                  kn_scale=1.0, eps_reg=1e-6, delta_floor=0.0, inv_mass=None, inv_inertia=None,
-                 contact_capacity=0, resort_every=0, level_ratio=0.0, stream=None, use_torch=True):
+                 contact_capacity=0, resort_every=0, level_ratio=0.0, lanes=0, stream=None,
+                 use_torch=True):
         self.lib = load()
         self._handle = C.c_void_p()
         x = _input(x, np.float64, (-1, 3))
@@ -213,6 +215,7 @@ class Bed:
         d.contact_capacity = int(contact_capacity)
         d.resort_every = int(resort_every)
         d.level_ratio = float(level_ratio)
+        d.lanes = int(lanes)
         self._alloc = None
         stream_ptr = None
         if use_torch:

@@ -46,7 +46,9 @@ def make_oracle(x, r, p, geoms=(), v=None, w=None):
 
 def make_gpu(x, r, p, geoms=(), v=None, w=None, **kw):
     from paper_2501_05300_gb300.dem import Bed
-    return Bed(x, np.asarray(r, np.float32), v=v, w=w, geoms=geoms, **p, **kw)
+    if not hasattr(r, "data_ptr"):
+        r = np.asarray(r, np.float32)
+    return Bed(x, r, v=v, w=w, geoms=geoms, **p, **kw)
 
 
 def canonical_gpu_contacts(a, b, lam):

@@ -115,28 +115,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def settle_and_place(torch, dem, spec, settle_steps):
-    """Settle the lattice (generation friction mu_t 0.1, mu_r 0.01, Sec. 3.1)
-    at dt = 2e-4 (Eq. 9 allows ~2.7e-4 for d = 5 mm under the bed's own
-    weight), then put the plate 0.1 mm above the surface under it."""
-    plate = spec.plate
-    geoms = [g for g in spec.geoms]
-    hold = beds.GeomSpec(**{**spec.geoms[plate].__dict__})
-    hold.c = (hold.c[0], hold.c[1], hold.c[2] + 1.0)          # out of the way while settling
-    geoms[plate] = hold
-    b = dem.Bed(spec.x, spec.r, geoms=geoms, rho=spec.material.rho, mu_t=0.1, mu_r=0.01,
-                n_it=N_IT, dt=2e-4)
-    b.step(settle_steps)
-    x, v, w = b.read_state()
-    b.close()
-    pc = spec.geoms[plate]
-    under = (x[:, 0] - pc.c[0]) ** 2 + (x[:, 1] - pc.c[1]) ** 2 <= pc.he[0] ** 2
-    top = float((x[under, 2] + spec.r[under]).max()) if under.any() else float((x[:, 2] + spec.r).max())
-    placed = beds.GeomSpec(**{**pc.__dict__})
-    placed.c = (pc.c[0], pc.c[1], top + 0.0001 + pc.he[2])
+def settle_and_place(dem, spec, settle_steps, lanes):
+    """Settle the lattice with the generation friction of Sec. 3.1 (mu_t 0.1,
+    mu_r 0.01) at dt = 2e-4 (Eq. 9 allows ~2.7e-4 for d = 5 mm under the bed's
+    own weight) with the plate lifted out of the way, then switch the same bed
+    to the test settings (dt 1e-5, mu_t 0.5, mu_r 0.02; warm starts kept) and
+    lower the plate onto the surface under it."""
+    pl = spec.plate
+    pc = spec.geoms[pl]
     geoms = list(spec.geoms)
-    geoms[plate] = placed
-    return x, v, w, geoms
+    hold = beds.GeomSpec(**{**pc.__dict__})
+    hold.c = (pc.c[0], pc.c[1], pc.c[2] + 1.0)
+    geoms[pl] = hold
+    m = spec.material
+    b = dem.Bed(spec.x, spec.r, geoms=geoms, rho=m.rho, mu_t=0.1, mu_r=0.01, n_it=N_IT, dt=2e-4,
+                lanes=lanes)
+    b.step(settle_steps)
+    b.set_params(dt=2e-4, n_it=N_IT, mu_t=m.mu_t, mu_r=m.mu_r, lanes=lanes)
+    b.step(100)                      # let the bed adapt to the test friction
+    b.set_params(dt=DT, n_it=N_IT, mu_t=m.mu_t, mu_r=m.mu_r, lanes=lanes)
+    b.step(50)
+    x, _, _ = b.read_state()
+    under = (x[:, 0] - pc.c[0]) ** 2 + (x[:, 1] - pc.c[1]) ** 2 <= pc.he[0] ** 2
+    top = float((x[under, 2] + spec.r[under]).max())
+    cur = b.read_geom(pl)
+    # move the plate down onto the surface in one step, then stop it
+    drop = (cur.c[2] - (top + pc.he[2])) / DT
+    b.apply_plate_velocity(pl, (0.0, 0.0, -drop))
+    b.step(1)
+    b.apply_plate_velocity(pl, (0.0, 0.0, 0.0))
+    return b, top
 
 
 def run_gpu(args, rank, world):
@@ -146,14 +154,8 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     dev = torch.cuda.current_device()
     spec = beds.refined_sinkage_bed()
-    x, v, w, geoms = settle_and_place(torch, dem, spec, args.settle)
-    m = spec.material
-    bed = dem.Bed(x, spec.r, v=v, w=w, geoms=geoms, rho=m.rho, mu_t=m.mu_t, mu_r=m.mu_r,
-                  n_it=N_IT, dt=DT, lanes=args.lanes)
+    bed, top = settle_and_place(dem, spec, args.settle, args.lanes)
     pl = spec.plate
-    # approach: bring the plate 0.2 mm into the surface (untimed), then 0.01 m/s
-    bed.apply_plate_velocity(pl, (0.0, 0.0, -0.05))
-    bed.step(600)
     bed.apply_plate_velocity(pl, (0.0, 0.0, -PLATE_V))
     bed.step(args.warmup)
     bed.sync()

@@ -94,7 +94,7 @@ typedef struct dem_bed_desc {
     int64_t contact_capacity;   /* sphere-sphere contacts; 0 = 8 n (grows never) */
     int32_t resort_every;       /* Morton re-sort period in steps; 0 = 20 */
     float level_ratio;          /* radius ratio per grid level; 0 = 2 */
-    int32_t lanes;              /* threads per particle in the Jacobi sweep: 1, 2, 4, 8; 0 = 4 */
+    int32_t lanes;              /* threads per particle in the Jacobi sweep: 1, 2, 4, 8; 0 = 2 */
     dem_alloc_fn alloc;         /* optional allocator (see above) */
     dem_free_fn free_fn;
     void* alloc_ctx;
@@ -164,6 +164,16 @@ dem_status dem_get_info(dem_bed* bed, dem_info* out);
  * the number of steps.  Synchronises. */
 dem_status dem_set_timing(dem_bed* bed, int32_t enable);
 dem_status dem_read_timing(dem_bed* bed, double* step_ms, double* jacobi_ms, int64_t* steps);
+
+/* Change the solver and material settings of an existing bed between steps,
+ * as between the generation and the test phases of Sec. 3.1 / 3.3 (reduced
+ * friction while settling).  Taken from `desc`: dt, n_it, damp_steps, e_H,
+ * mu_t, mu_r, gravity, kn_scale, eps_reg and lanes; every other field is
+ * ignored.  The warm-start impulses of the last step are rescaled by
+ * dt_new / dt_old so that they stand for the same forces, and the sinkage
+ * reference of every primitive is re-taken from the current particle surface
+ * (the test phase starts here).  Synchronises; the per-step graphs are rebuilt. */
+dem_status dem_set_params(dem_bed* bed, const dem_bed_desc* desc);
 
 /* Release all device memory of the bed.  NULL is accepted. */
 dem_status dem_destroy_bed(dem_bed* bed);

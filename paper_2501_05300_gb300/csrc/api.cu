@@ -116,6 +116,36 @@ static double estar(double E1, double nu1, double E2, double nu2) {
 
 static dem_status build_graphs(dem_bed* b);
 
+// Height of the particle surface under each primitive: the highest top z + r
+// of the particles whose centre lies inside the primitive's footprint in x, y
+// (all particles if none does).  pos/rad are read with the given strides.
+static void surface_refs(int n, const double* pos, int ps, const double* rad, int rs, int ng,
+                         const int* type, const double* c, const double* R, const double* he,
+                         std::vector<double>& out) {
+    out.assign(ng, 0.0);
+    double ztop_all = -1e300;
+    for (int i = 0; i < n; ++i) ztop_all = std::max(ztop_all, pos[ps * i + 2] + rad[rs * i]);
+    for (int g = 0; g < ng; ++g) {
+        double zr = -1e300;
+        for (int i = 0; i < n; ++i) {
+            const double dx = pos[ps * i] - c[3 * g], dy = pos[ps * i + 1] - c[3 * g + 1];
+            bool under = false;
+            if (type[g] == DEM_GEOM_CYLINDER) {
+                under = dx * dx + dy * dy <= he[3 * g] * he[3 * g];
+            } else if (type[g] == DEM_GEOM_BOX) {
+                double ex = 0, ey = 0;
+                for (int k = 0; k < 3; ++k) {
+                    ex += std::fabs(R[9 * g + k]) * he[3 * g + k];
+                    ey += std::fabs(R[9 * g + 3 + k]) * he[3 * g + k];
+                }
+                under = std::fabs(dx) <= ex && std::fabs(dy) <= ey;
+            }
+            if (under) zr = std::max(zr, pos[ps * i + 2] + rad[rs * i]);
+        }
+        out[g] = zr > -1e299 ? zr : ztop_all;
+    }
+}
+
 extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_bed** out) {
     g_err.clear();
     if (!out) return fail(DEM_ERR_ARG, "out is NULL");
@@ -249,7 +279,7 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     if (cap > (int64_t)0x3fffffff) cap = 0x3fffffff;
     P.max_contacts = (int)cap;
     P.max_geo = 2 * n + 1024;
-    P.lanes = d->lanes > 0 ? d->lanes : 4;
+    P.lanes = d->lanes > 0 ? d->lanes : 2;
     if (P.lanes != 1 && P.lanes != 2 && P.lanes != 4 && P.lanes != 8) {
         release(b);
         return fail(DEM_ERR_ARG, "lanes = %d is not 1, 2, 4 or 8", d->lanes);
@@ -295,27 +325,16 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     P.n_cells = (int)total_cells;
 
     // sinkage references: highest particle top under each primitive's footprint
-    b->z_ref.assign(P.ng, 0.0);
-    double ztop_all = -1e300;
-    for (int i = 0; i < n; ++i) ztop_all = std::max(ztop_all, pos[3 * i + 2] + rad[i]);
-    for (int g = 0; g < P.ng; ++g) {
-        const dem_geom& G = d->geom[g];
-        double zr = -1e300;
-        for (int i = 0; i < n; ++i) {
-            const double dx = pos[3 * i] - G.c[0], dy = pos[3 * i + 1] - G.c[1];
-            bool under = false;
-            if (G.type == DEM_GEOM_CYLINDER) under = dx * dx + dy * dy <= G.he[0] * G.he[0];
-            else if (G.type == DEM_GEOM_BOX) {
-                double ex = 0, ey = 0;
-                for (int k = 0; k < 3; ++k) {
-                    ex += std::fabs(G.R[k]) * G.he[k];
-                    ey += std::fabs(G.R[3 + k]) * G.he[k];
-                }
-                under = std::fabs(dx) <= ex && std::fabs(dy) <= ey;
-            }
-            if (under) zr = std::max(zr, pos[3 * i + 2] + rad[i]);
+    {
+        std::vector<int> types(P.ng);
+        std::vector<double> gc(3 * (size_t)P.ng), gR(9 * (size_t)P.ng), ghe(3 * (size_t)P.ng);
+        for (int g = 0; g < P.ng; ++g) {
+            types[g] = d->geom[g].type;
+            for (int k = 0; k < 3; ++k) { gc[3 * g + k] = d->geom[g].c[k]; ghe[3 * g + k] = d->geom[g].he[k]; }
+            for (int k = 0; k < 9; ++k) gR[9 * g + k] = d->geom[g].R[k];
         }
-        b->z_ref[g] = zr > -1e299 ? zr : ztop_all;
+        std::vector<double> rr(rad.begin(), rad.end());
+        surface_refs(n, pos.data(), 3, rr.data(), 1, P.ng, types.data(), gc.data(), gR.data(), ghe.data(), b->z_ref);
     }
 
     // ---- device memory ----
@@ -784,6 +803,68 @@ extern "C" dem_status dem_read_timing(dem_bed* b, double* step_ms, double* jacob
     if (jacobi_ms) *jacobi_ms = b->t_jac_ms;
     if (steps) *steps = b->t_steps;
     return DEM_OK;
+}
+
+// scale the impulses of the last step (the next warm start) by s
+__global__ void k_rescale_warm(DevBuf B, int p, int n, float s, int cap, int gcap) {
+    const int nc = min(B.own_start[p][n], cap), ng = min(B.geo_start[p][n], gcap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * (nc + ng); k += gridDim.x * blockDim.x) {
+        float4* q = k < 2 * nc ? &B.lamW[p][k] : &B.glamW[p][k - 2 * nc];
+        float4 v = *q;
+        *q = make_float4(v.x * s, v.y * s, v.z * s, v.w * s);
+    }
+}
+
+extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
+    g_err.clear();
+    if (!b || !d) return fail(DEM_ERR_ARG, "NULL argument");
+    if (b->faulted) return fail(DEM_ERR_STATE, "the bed holds a latched device fault");
+    if (!(d->dt > 0.f) || d->n_it < 0 || !(d->e_H >= 1.f) || d->damp_steps < 0.f || d->mu_t < 0.f ||
+        d->mu_r < 0.f || d->eps_reg < 0.f)
+        return fail(DEM_ERR_ARG, "invalid solver or material settings");
+    const int lanes = d->lanes > 0 ? d->lanes : b->P.lanes;
+    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return fail(DEM_ERR_ARG, "bad lanes");
+    CK(cudaSetDevice(b->dev));
+    SimParams& P = b->P;
+    const float scale = d->dt / P.dt;
+    if (b->steps > 0 && P.n > 0 && scale != 1.0f) {
+        const int p = (int)((b->steps - 1) & 1);
+        k_rescale_warm<<<256, 256, 0, b->stream>>>(b->B, p, P.n, scale, P.max_contacts, P.max_geo);
+        CK(cudaGetLastError());
+    }
+    P.n_it = d->n_it;
+    P.dt = d->dt;
+    P.inv_dt = 1.0f / d->dt;
+    P.e_H = d->e_H;
+    P.kn_scale = d->kn_scale > 0.f ? d->kn_scale : 1.0f;
+    P.eps_reg = d->eps_reg;
+    P.ups = 1.0f / (1.0f + 4.0f * d->damp_steps);
+    P.mu_t = d->mu_t;
+    P.mu_r = d->mu_r;
+    P.gx = d->gravity[0]; P.gy = d->gravity[1]; P.gz = d->gravity[2];
+    P.lanes = lanes;
+    CK(cudaStreamSynchronize(b->stream));
+    // the test phase starts here: re-take the surface under every primitive
+    if (P.n > 0 && P.ng > 0) {
+        std::vector<double4_32a> hp(P.n);
+        std::vector<GeomDev> hg(P.ng);
+        CK(cudaMemcpy(hp.data(), b->B.pos, P.n * sizeof(double4_32a), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(hg.data(), b->B.geom, P.ng * sizeof(GeomDev), cudaMemcpyDeviceToHost));
+        std::vector<int> types(P.ng);
+        std::vector<double> gc(3 * (size_t)P.ng), gR(9 * (size_t)P.ng), ghe(3 * (size_t)P.ng);
+        for (int g = 0; g < P.ng; ++g) {
+            types[g] = hg[g].type;
+            for (int k = 0; k < 3; ++k) { gc[3 * g + k] = hg[g].c[k]; ghe[3 * g + k] = hg[g].he[k]; }
+            for (int k = 0; k < 9; ++k) gR[9 * g + k] = hg[g].R[k];
+        }
+        surface_refs(P.n, &hp[0].x, 4, &hp[0].w, 4, P.ng, types.data(), gc.data(), gR.data(), ghe.data(),
+                     b->z_ref);
+    }
+    for (int p = 0; p < 2; ++p)
+        for (int k = 0; k < 3; ++k)
+            if (b->g[p][k]) { cudaGraphExecDestroy(b->g[p][k]); b->g[p][k] = nullptr; }
+    if (b->g_resort) { cudaGraphExecDestroy(b->g_resort); b->g_resort = nullptr; }
+    return build_graphs(b);
 }
 
 extern "C" dem_status dem_destroy_bed(dem_bed* b) {

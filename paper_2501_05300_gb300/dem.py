@@ -26,7 +26,7 @@ PLANE, BOX, CYLINDER = 0, 1, 2
 # every entry point declared in include/dem.h
 EXPORTS = ("dem_create_bed", "dem_step", "dem_apply_plate_velocity", "dem_read_forces",
            "dem_read_state", "dem_read_contacts", "dem_read_geom", "dem_sync", "dem_get_info",
-           "dem_set_timing", "dem_read_timing", "dem_destroy_bed", "dem_last_error")
+           "dem_set_timing", "dem_read_timing", "dem_set_params", "dem_destroy_bed", "dem_last_error")
 
 
 class DemError(RuntimeError):
@@ -105,6 +105,7 @@ def load(build: bool = True):
         "dem_get_info": (i32, [vp, C.POINTER(dem_info)]),
         "dem_set_timing": (i32, [vp, i32]),
         "dem_read_timing": (i32, [vp, dp, dp, C.POINTER(C.c_int64)]),
+        "dem_set_params": (i32, [vp, C.POINTER(dem_bed_desc)]),
         "dem_destroy_bed": (i32, [vp]),
         "dem_last_error": (C.c_char_p, []),
     }
@@ -287,6 +288,16 @@ class Bed:
         a, j, s = C.c_double(), C.c_double(), C.c_int64()
         _check(self.lib.dem_read_timing(self._handle, C.byref(a), C.byref(j), C.byref(s)))
         return a.value, j.value, s.value
+
+    def set_params(self, *, dt, n_it, mu_t, mu_r, damp_steps=4.5, e_H=1.25, gravity=(0.0, 0.0, -9.81),
+                   kn_scale=1.0, eps_reg=1e-6, lanes=0):
+        """Change solver and material settings between steps (dem_set_params)."""
+        d = dem_bed_desc()
+        d.dt, d.n_it, d.mu_t, d.mu_r, d.damp_steps, d.e_H = dt, int(n_it), mu_t, mu_r, damp_steps, e_H
+        d.gravity = (C.c_float * 3)(*map(float, gravity))
+        d.kn_scale, d.eps_reg, d.lanes = kn_scale, eps_reg, int(lanes)
+        _check(self.lib.dem_set_params(self._handle, C.byref(d)))
+        self.dt = dt
 
     def close(self):
         if getattr(self, "_handle", None) and self._handle.value:

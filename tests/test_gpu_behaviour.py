@@ -134,3 +134,27 @@ def test_torch_device_buffers_are_accepted():
     assert np.array_equal(g1.read_state()[1], g2.read_state()[1])
     g1.close()
     g2.close()
+
+
+def test_set_params_keeps_state_and_rescales_warm_start():
+    x, r = compressed_cloud(1500, seed=13)
+    lo, hi = x.min(0) - 0.004, x.max(0) + 0.004
+    p = params(n_it=30)
+    g1 = make_gpu(x, r, p, box_geoms(lo, hi))
+    g2 = make_gpu(x, r, p, box_geoms(lo, hi))
+    g1.step(10)
+    g2.step(10)
+    # the same settings again: the graphs are rebuilt, nothing else changes
+    g2.set_params(dt=p["dt"], n_it=30, mu_t=p["mu_t"], mu_r=p["mu_r"])
+    g1.step(10)
+    g2.step(10)
+    assert np.array_equal(g1.read_state()[1], g2.read_state()[1])
+    # a new time step rescales the stored impulses by dt_new / dt_old
+    a, b, lam, _ = g2.read_contacts()
+    g2.set_params(dt=2 * p["dt"], n_it=30, mu_t=p["mu_t"], mu_r=p["mu_r"])
+    a2, b2, lam2, _ = g2.read_contacts()
+    assert np.array_equal(a, a2) and np.allclose(lam2, 2 * lam, rtol=1e-7, atol=0)
+    g2.step(5)
+    g2.sync()
+    g1.close()
+    g2.close()

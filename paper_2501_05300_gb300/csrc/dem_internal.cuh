@@ -166,7 +166,7 @@ static __device__ __forceinline__ float3 cross(float3 a, float3 b) {
 // Basis, Revisited", JCGT 6(1), 2017.
 static __device__ __forceinline__ void tangent_basis(float3 n, float3& t1, float3& t2) {
     float sg = copysignf(1.0f, n.z);
-    float a = -1.0f / (sg + n.z);
+    float a = -__frcp_rn(sg + n.z);
     float b = n.x * n.y * a;
     t1 = make_float3(1.0f + sg * n.x * n.x * a, sg * b, -sg * n.x);
     t2 = make_float3(b, sg + n.y * n.y * a, -n.y);

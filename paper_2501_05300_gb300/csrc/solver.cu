@@ -195,7 +195,7 @@ static __device__ __forceinline__ Upd contact_update(float4 r0, float4 r1, float
     const float bt = mu_t * u.pn;
     const float m2 = pt1 * pt1 + pt2 * pt2;
     if (m2 > bt * bt) {   // Coulomb disc (Eq. 6)
-        const float s = bt / sqrtf(m2);
+        const float s = bt * rsqrtf(m2);
         pt1 *= s;
         pt2 *= s;
     }
@@ -206,7 +206,7 @@ static __device__ __forceinline__ Upd contact_update(float4 r0, float4 r1, float
     float3 pr = pr0 - r1.w * ((wa - wb) + sig_t * pr0);
     const float br = mur * u.pn;
     const float q2 = dot(pr, pr);
-    if (q2 > br * br) pr = (br / sqrtf(q2)) * pr;
+    if (q2 > br * br) pr = (br * rsqrtf(q2)) * pr;
     u.pr = pr;
     return u;
 }
@@ -248,8 +248,11 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
         wi4 = win[i];
         const float3 vi = f3(vi4), wi = f3(wi4);
         const int e1 = B.inc_start[i + 1];
-        for (int e = B.inc_start[i] + lane; e < e1; e += T) {
-            const int2 ent = B.inc[e];
+        int e = B.inc_start[i] + lane;
+        int2 nxt = e < e1 ? B.inc[e] : make_int2(0, 0);
+        for (; e < e1; e += T) {
+            const int2 ent = nxt;
+            if (e + T < e1) nxt = B.inc[e + T];   // fetch the next entry before this one's data
             const bool sideb = ent.x < 0;
             const int c = ent.x & 0x7fffffff;
             const float4 r0 = B.rec[3 * (size_t)c], r2 = B.rec[3 * (size_t)c + 2];

@@ -178,6 +178,28 @@ dem_status dem_set_params(dem_bed* bed, const dem_bed_desc* desc);
 /* Release all device memory of the bed.  NULL is accepted. */
 dem_status dem_destroy_bed(dem_bed* bed);
 
+/* Sphere-sphere contacts of n spheres, for callers that may not allocate GPU
+ * memory: a host program whose device memory is held by another framework's
+ * caching allocator, a real-time loop that forbids allocation after start-up,
+ * or code enqueuing work while a stream is being captured.  The paper has no
+ * counterpart: it is a service entry point of this library.
+ *   pos [3n] double, radius [n] float: device memory, read only.
+ *   key_a, key_b [cap] int32, delta [cap] float: device memory; contact k is the
+ *     pair (key_a[k] < key_b[k]) of input indices with overlap delta[k] > 0, found
+ *     with the same exact predicate as dem_step; order unspecified.
+ *   count: device int64, receives the number of contacts (may exceed cap; only
+ *     the first cap are written).
+ *   stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
+ * Allocates nothing: every intermediate array lives in one static device array
+ * of about 8.4 MB, present on every GPU that loads the library until the process
+ * exits.  n must be <= 262144 (DEM_ERR_ARG otherwise).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU race: order them on one stream. */
+dem_status dem_detect_contacts_noalloc(int32_t n, const double* pos, const float* radius, int64_t cap,
+                                       int32_t* key_a, int32_t* key_b, float* delta, int64_t* count,
+                                       void* stream);
+
 /* Thread-local description of the last error ("" if none). */
 const char* dem_last_error(void);
 

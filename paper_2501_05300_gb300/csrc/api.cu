@@ -874,3 +874,6 @@ extern "C" dem_status dem_destroy_bed(dem_bed* b) {
 }
 
 extern "C" const char* dem_last_error(void) { return g_err.c_str(); }
+
+// lets other translation units report through dem_last_error()
+void dem_set_error_message(const char* msg) { g_err = msg; }

@@ -26,7 +26,8 @@ PLANE, BOX, CYLINDER = 0, 1, 2
 # every entry point declared in include/dem.h
 EXPORTS = ("dem_create_bed", "dem_step", "dem_apply_plate_velocity", "dem_read_forces",
            "dem_read_state", "dem_read_contacts", "dem_read_geom", "dem_sync", "dem_get_info",
-           "dem_set_timing", "dem_read_timing", "dem_set_params", "dem_destroy_bed", "dem_last_error")
+           "dem_set_timing", "dem_read_timing", "dem_set_params", "dem_destroy_bed",
+           "dem_detect_contacts_noalloc", "dem_last_error")
 
 
 class DemError(RuntimeError):
@@ -107,6 +108,7 @@ def load(build: bool = True):
         "dem_read_timing": (i32, [vp, dp, dp, C.POINTER(C.c_int64)]),
         "dem_set_params": (i32, [vp, C.POINTER(dem_bed_desc)]),
         "dem_destroy_bed": (i32, [vp]),
+        "dem_detect_contacts_noalloc": (i32, [i32, vp, vp, i64, vp, vp, vp, vp, vp]),
         "dem_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sigs.items():
@@ -309,6 +311,17 @@ class Bed:
             self.close()
         except Exception:
             pass
+
+
+def detect_contacts_noalloc(pos, radius, key_a, key_b, delta, count, stream=None):
+    """dem_detect_contacts_noalloc on torch CUDA tensors (pos float64 [n,3],
+    radius float32 [n], outputs int32/int32/float32 [cap], count int64 [1]).
+    The library allocates nothing; the caller owns every buffer."""
+    lib = load()
+    n = int(radius.shape[0])
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.dem_detect_contacts_noalloc(n, _ptr(pos), _ptr(radius), int(key_a.shape[0]), _ptr(key_a),
+                                           _ptr(key_b), _ptr(delta), _ptr(count), sp))
 
 
 def bed_from(spec, *, n_it, dt, **kw) -> Bed:

@@ -94,7 +94,8 @@ typedef struct dem_bed_desc {
     int64_t contact_capacity;   /* sphere-sphere contacts; 0 = 8 n (grows never) */
     int32_t resort_every;       /* Morton re-sort period in steps; 0 = 20 */
     float level_ratio;          /* radius ratio per grid level; 0 = 2 */
-    int32_t lanes;              /* threads per particle in the Jacobi sweep: 1, 2, 4, 8; 0 = 2 */
+    int32_t lanes;              /* Jacobi sweep layout: 0 = contact pass + body pass (default);
+                                   1, 2, 4, 8 = one kernel with that many threads per particle */
     dem_alloc_fn alloc;         /* optional allocator (see above) */
     dem_free_fn free_fn;
     void* alloc_ctx;

@@ -279,8 +279,8 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     if (cap > (int64_t)0x3fffffff) cap = 0x3fffffff;
     P.max_contacts = (int)cap;
     P.max_geo = 2 * n + 1024;
-    P.lanes = d->lanes > 0 ? d->lanes : 2;
-    if (P.lanes != 1 && P.lanes != 2 && P.lanes != 4 && P.lanes != 8) {
+    P.lanes = d->lanes;   // 0: two-pass sweep; 1, 2, 4, 8: one kernel, that many threads per body
+    if (P.lanes != 0 && P.lanes != 1 && P.lanes != 2 && P.lanes != 4 && P.lanes != 8) {
         release(b);
         return fail(DEM_ERR_ARG, "lanes = %d is not 1, 2, 4 or 8", d->lanes);
     }
@@ -356,6 +356,7 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     AL(B.c_other, C); AL(B.c_key[0], C); AL(B.c_key[1], C); AL(B.rec, 3 * C); AL(B.c_delta, C);
     AL(B.lamA[0], C); AL(B.lamA[1], C); AL(B.lamB[0], C); AL(B.lamB[1], C);
     AL(B.lamW[0], 2 * C); AL(B.lamW[1], 2 * C); AL(B.inc, 2 * C);
+    AL(B.c_self, C); AL(B.c_pos, C); AL(B.impA, 2 * C); AL(B.impB, 2 * C);
     AL(B.g_key[0], GC); AL(B.g_key[1], GC); AL(B.grec, 6 * GC); AL(B.g_delta, GC);
     AL(B.glamA[0], GC); AL(B.glamA[1], GC); AL(B.glamB[0], GC); AL(B.glamB[1], GC);
     AL(B.glamW[0], 2 * GC); AL(B.glamW[1], 2 * GC);
@@ -822,8 +823,8 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
     if (!(d->dt > 0.f) || d->n_it < 0 || !(d->e_H >= 1.f) || d->damp_steps < 0.f || d->mu_t < 0.f ||
         d->mu_r < 0.f || d->eps_reg < 0.f)
         return fail(DEM_ERR_ARG, "invalid solver or material settings");
-    const int lanes = d->lanes > 0 ? d->lanes : b->P.lanes;
-    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return fail(DEM_ERR_ARG, "bad lanes");
+    const int lanes = d->lanes >= 0 ? d->lanes : b->P.lanes;
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return fail(DEM_ERR_ARG, "bad lanes");
     CK(cudaSetDevice(b->dev));
     SimParams& P = b->P;
     const float scale = d->dt / P.dt;

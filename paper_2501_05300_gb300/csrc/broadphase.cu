@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(BP_T) k_contacts_build(SimParams P, DevBuf B, 
         if (c >= P.max_contacts) { set_flag(B.err, DEM_FLAG_CAPACITY); break; }
         const int2 e = own[k];
         B.c_other[c] = e.x;
+        B.c_self[c] = i;
         B.c_key[parity][c] = e.y;
         if (is + k < inc_cap) B.inc[is + k] = make_int2(c, e.x);
         const int slot = atomicAdd(&B.in_fill[e.x], 1);
@@ -151,35 +152,43 @@ __global__ void __launch_bounds__(BP_T) k_contacts_build(SimParams P, DevBuf B, 
     }
 }
 
-// Sort every incidence list by the stable id of the other body.
+// Sort every incidence list by the stable id of the other body, then record
+// where each contact sits in the lists of its two bodies.
 __global__ void __launch_bounds__(BP_T) k_inc_sort(SimParams P, DevBuf B) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n || *B.err) return;
     const int s = B.inc_start[i], e = B.inc_start[i + 1];
     const int m = e - s;
     const int no = B.own_cnt[i];
-    if (m - no <= 0) return;   // only owned entries, already sorted
     int2* L = B.inc + s;
-    if (m <= 24) {
-        int2 ent[24];
-        int key[24];
-        for (int k = 0; k < m; ++k) {
-            int2 v = L[k];
-            int q = k;
-            int kv = B.id[v.y];
-            while (q > 0 && key[q - 1] > kv) { ent[q] = ent[q - 1]; key[q] = key[q - 1]; --q; }
-            ent[q] = v;
-            key[q] = kv;
+    if (m - no > 0) {   // incoming entries present: the list needs sorting
+        if (m <= 24) {
+            int2 ent[24];
+            int key[24];
+            for (int k = 0; k < m; ++k) {
+                int2 v = L[k];
+                int q = k;
+                int kv = B.id[v.y];
+                while (q > 0 && key[q - 1] > kv) { ent[q] = ent[q - 1]; key[q] = key[q - 1]; --q; }
+                ent[q] = v;
+                key[q] = kv;
+            }
+            for (int k = 0; k < m; ++k) L[k] = ent[k];
+        } else {
+            for (int k = 1; k < m; ++k) {
+                int2 v = L[k];
+                int kv = B.id[v.y];
+                int q = k;
+                while (q > 0 && B.id[L[q - 1].y] > kv) { L[q] = L[q - 1]; --q; }
+                L[q] = v;
+            }
         }
-        for (int k = 0; k < m; ++k) L[k] = ent[k];
-    } else {
-        for (int k = 1; k < m; ++k) {
-            int2 v = L[k];
-            int kv = B.id[v.y];
-            int q = k;
-            while (q > 0 && B.id[L[q - 1].y] > kv) { L[q] = L[q - 1]; --q; }
-            L[q] = v;
-        }
+    }
+    for (int k = 0; k < m; ++k) {
+        const int2 v = L[k];
+        const int c = v.x & 0x7fffffff;
+        if (v.x < 0) B.c_pos[c].y = s + k;
+        else B.c_pos[c].x = s + k;
     }
 }
 

@@ -107,6 +107,10 @@ struct DevBuf {
     float2* lamB[2];
     float4* lamW[2];    // [2C] world-frame final impulses, per parity
     int2* inc;          // [2C]
+    int* c_self;        // [C] slot of body a (the owner)
+    int2* c_pos;        // [C] positions of the contact in a's and b's incidence lists
+    float4* impA;       // [2C] per incidence entry: impulse share (P.x, P.y, P.z, T.x)
+    float2* impB;       // [2C] (T.y, T.z)
     // sphere-geometry contacts (one-sided)
     int* g_key[2];      // [max_geo] primitive index, per parity
     float4* grec;       // [6 * max_geo]

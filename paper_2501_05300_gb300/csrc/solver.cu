@@ -20,6 +20,8 @@
 // bodies' previous iterates -- the same arithmetic on the same inputs at both
 // ends, so both ends agree bit for bit -- writes it if it owns the contact and
 // adds its own share of the impulse.  One kernel per sweep, no atomics.
+#include <algorithm>
+
 #include "dem_internal.cuh"
 #include "geometry.cuh"
 
@@ -397,6 +399,123 @@ int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s
     k_setup<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity);
     return 1;
 }
+// ---------------------------------------------------------------------------
+// Two-pass sweep.  Contact pass: one thread per contact computes its update
+// once from the two bodies' previous iterates, stores the new impulse and the
+// impulse share of each body at the contact's position in that body's
+// incidence list.  Body pass: each body adds its shares in list order (stable
+// id of the other body), updates its geometry contacts, and forms
+// v = v* + M^-1 sum.  Successive passes are chained with programmatic
+// dependent launch: a pass may start while the previous one drains and waits
+// (griddepcontrol.wait) before reading what it produced.
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+static __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+template <bool LAST>
+__global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, int p, int src) {
+    pdl_wait();
+    pdl_trigger();
+    if (*B.err) return;
+    const int dst = src ^ 1;
+    const int nc = min(B.own_start[p][P.n], P.max_contacts);
+    const float4* __restrict__ vin = B.vel[src];
+    const float4* __restrict__ win = B.omg[src];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const int a = B.c_self[c], b = B.c_other[c];
+        const int2 pos = B.c_pos[c];
+        const float4 r0 = B.rec[3 * (size_t)c], r1 = B.rec[3 * (size_t)c + 1], r2 = B.rec[3 * (size_t)c + 2];
+        const float4 l0 = B.lamA[src][c];
+        const float2 l1 = B.lamB[src][c];
+        const float3 va = f3(vin[a]), wa = f3(win[a]), vb = f3(vin[b]), wb = f3(win[b]);
+        const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, va - vb, wa, wb, P.eps_reg);
+        const float3 n = f3(r0);
+        if (LAST) {
+            write_world(B.lamW[p], c, n, u);
+        } else {
+            B.lamA[dst][c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+            B.lamB[dst][c] = make_float2(u.pr.y, u.pr.z);
+        }
+        float3 La = make_float3(0.f, 0.f, 0.f), Aa = La, Lb = La, Ab = La;
+        add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
+        add_impulse(n, u.t1, u.t2, r2.y, u.pn, u.pt1, u.pt2, u.pr, true, Lb, Ab);
+        B.impA[pos.x] = make_float4(La.x, La.y, La.z, Aa.x);
+        B.impB[pos.x] = make_float2(Aa.y, Aa.z);
+        B.impA[pos.y] = make_float4(Lb.x, Lb.y, Lb.z, Ab.x);
+        B.impB[pos.y] = make_float2(Ab.y, Ab.z);
+    }
+}
+
+template <bool LAST>
+__global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p, int src) {
+    pdl_wait();
+    pdl_trigger();
+    if (*B.err) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const int dst = src ^ 1;
+    float3 accL = make_float3(0.f, 0.f, 0.f), accA = accL;
+    const int e1 = B.inc_start[i + 1];
+    for (int e = B.inc_start[i]; e < e1; ++e) {
+        const float4 q = B.impA[e];
+        const float2 t = B.impB[e];
+        accL = accL + f3(q);
+        accA = accA + make_float3(q.w, t.x, t.y);
+    }
+    const int g1 = B.geo_start[p][i + 1];
+    int k = B.geo_start[p][i];
+    if (k < g1) {
+        const float3 vi = f3(B.vel[src][i]), wi = f3(B.omg[src][i]);
+        for (; k < g1; ++k) {
+            const float4* r = B.grec + 6 * (size_t)k;
+            const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+            const float4 l0 = B.glamA[src][k];
+            const float2 l1 = B.glamB[src][k];
+            const float3 n = f3(r0);
+            const Upd u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4), P.eps_reg);
+            if (LAST) {
+                write_world(B.glamW[p], k, n, u);
+            } else {
+                B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+                B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
+            }
+            add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
+        }
+    }
+    const float4 v0 = B.vel0[i], w0 = B.omg0[i];
+    const float gm = v0.w > 0.0f ? P.dt : 0.0f;
+    const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
+    const float3 v = vs + v0.w * accL;
+    const float3 w = f3(w0) + w0.w * accA;
+    B.vel[dst][i] = make_float4(v.x, v.y, v.z, v0.w);
+    B.omg[dst][i] = make_float4(w.x, w.y, w.z, w0.w);
+}
+
+template <typename K>
+static void launch_pdl(K kernel, int blocks, cudaStream_t s, const SimParams& P, const DevBuf& B, int p, int src) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(SV_T);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, P, B, p, src);
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
 template <int T>
 static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int src, bool update, bool last,
                          int write_final, cudaStream_t s) {
@@ -408,7 +527,7 @@ static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int sr
 
 static void sweep_dispatch(const SimParams& P, const DevBuf& B, int parity, int src, bool update, bool last,
                            int write_final, cudaStream_t s) {
-    switch (P.lanes) {
+    switch (P.lanes > 0 ? P.lanes : 2) {
         case 1: sweep_launch<1>(P, B, parity, src, update, last, write_final, s); break;
         case 2: sweep_launch<2>(P, B, parity, src, update, last, write_final, s); break;
         case 8: sweep_launch<8>(P, B, parity, src, update, last, write_final, s); break;
@@ -422,8 +541,23 @@ int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
     return 1;
 }
 int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s) {
-    sweep_dispatch(P, B, parity, it & 1, true, it == P.n_it - 1, 0, s);
-    return 1;
+    const int src = it & 1;
+    const bool last = it == P.n_it - 1;
+    if (P.lanes > 0) {   // single-kernel sweep, T threads per body
+        sweep_dispatch(P, B, parity, src, true, last, 0, s);
+        return 1;
+    }
+    // two-pass sweep: contacts (grid-stride over the capacity) then bodies
+    const int cblocks = std::min(nblk(P.max_contacts, SV_T), 16 * sm_count());
+    const int bblocks = nblk(P.n, SV_T);
+    if (last) {
+        launch_pdl(k_contact_pass<true>, cblocks, s, P, B, parity, src);
+        launch_pdl(k_body_pass<true>, bblocks, s, P, B, parity, src);
+    } else {
+        launch_pdl(k_contact_pass<false>, cblocks, s, P, B, parity, src);
+        launch_pdl(k_body_pass<false>, bblocks, s, P, B, parity, src);
+    }
+    return 2;
 }
 int launch_integrate(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
     k_integrate<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity, P.n_it & 1);

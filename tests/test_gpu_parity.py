@@ -125,7 +125,7 @@ def test_settling_trajectory_200_steps():
     g.close()
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8])
 def test_dense_trajectory_200_steps(lanes):
     """A compressed cloud in a box under gravity expands and collides for 200
     steps with warm starts; every sweep variant (threads per particle)."""

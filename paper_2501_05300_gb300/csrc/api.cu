@@ -344,8 +344,7 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     const int nbr = radix_blocks(n);
     dem_status st = DEM_OK;
 #define AL(ptr, cnt) if (st == DEM_OK) st = dalloc_n(b, &(ptr), (cnt))
-    AL(B.pos, N); AL(B.posr, N); AL(B.vel0, N); AL(B.omg0, N);
-    AL(B.vel[0], N); AL(B.vel[1], N); AL(B.omg[0], N); AL(B.omg[1], N);
+    AL(B.pos, N); AL(B.posr, N); AL(B.vw0, N); AL(B.vw[0], N); AL(B.vw[1], N);
     AL(B.id, N); AL(B.lvl, N); AL(B.prev_of, N); AL(B.resorted, 1); AL(B.err, 1);
     AL(B.body_cell, N); AL(B.cell_cnt, NC + 1); AL(B.cell_start, NC + 1); AL(B.cell_fill, NC + 1);
     AL(B.cell_body, N);
@@ -356,14 +355,14 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     AL(B.c_other, C); AL(B.c_key[0], C); AL(B.c_key[1], C); AL(B.rec, 3 * C); AL(B.c_delta, C);
     AL(B.lamA[0], C); AL(B.lamA[1], C); AL(B.lamB[0], C); AL(B.lamB[1], C);
     AL(B.lamW[0], 2 * C); AL(B.lamW[1], 2 * C); AL(B.inc, 2 * C);
-    AL(B.c_self, C); AL(B.c_pos, C); AL(B.impA, 2 * C); AL(B.impB, 2 * C);
+    AL(B.c_self, C); AL(B.c_pos, C); AL(B.imp, 2 * C);
     AL(B.g_key[0], GC); AL(B.g_key[1], GC); AL(B.grec, 6 * GC); AL(B.g_delta, GC);
     AL(B.glamA[0], GC); AL(B.glamA[1], GC); AL(B.glamB[0], GC); AL(B.glamB[1], GC);
     AL(B.glamW[0], 2 * GC); AL(B.glamW[1], 2 * GC);
     AL(B.geom, (size_t)std::max(P.ng, 1)); AL(B.gacc, 6 * (size_t)std::max(P.ng, 1));
     AL(B.key_a, N); AL(B.key_b, N); AL(B.val_a, N); AL(B.val_b, N);
     AL(B.hist, 256 * (size_t)nbr + 1);
-    AL(B.t_pos, N); AL(B.t_v, N); AL(B.t_w, N); AL(B.t_id, N); AL(B.t_lvl, N);
+    AL(B.t_pos, N); AL(B.t_vw, N); AL(B.t_id, N); AL(B.t_lvl, N);
     // scan scratch: tile totals of up to 3 columns over the largest scanned array
     const size_t scan_n = std::max({NC + 1, N + 1, 256 * (size_t)nbr + 1});
     AL(B.scan_tmp, 3 * (scan_n / 2048 + 2));
@@ -375,13 +374,14 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
 
     // ---- upload ----
     std::vector<double4_32a> hp(N);
-    std::vector<float4> hr(N), hv(N), hw(N);
+    std::vector<float4> hr(N);
+    std::vector<VW> hv(N);
     std::vector<int> hid(N), hl(N);
     for (int i = 0; i < n; ++i) {
         hp[i] = make_double4_32a(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], (double)rad[i]);
         hr[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], rad[i]);
-        hv[i] = make_float4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], im[i]);
-        hw[i] = make_float4(omg[3 * i], omg[3 * i + 1], omg[3 * i + 2], iI[i]);
+        hv[i].v = make_float4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], im[i]);
+        hv[i].w = make_float4(omg[3 * i], omg[3 * i + 1], omg[3 * i + 2], iI[i]);
         hid[i] = i;
         hl[i] = lvl[i];
     }
@@ -402,8 +402,7 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     cudaStream_t s = b->stream;
     CK(cudaMemcpyAsync(B.pos, hp.data(), N * sizeof(double4_32a), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.posr, hr.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(B.vel0, hv.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(B.omg0, hw.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.vw0, hv.data(), N * sizeof(VW), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.id, hid.data(), N * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.lvl, hl.data(), N * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.geom, hg.data(), hg.size() * sizeof(GeomDev), cudaMemcpyHostToDevice, s));
@@ -666,12 +665,11 @@ extern "C" dem_status dem_read_state(dem_bed* b, double* pos, float* vel, float*
     CK(cudaSetDevice(b->dev));
     if (n == 0) return check_fault(b);
     std::vector<double4_32a> hp(n);
-    std::vector<float4> hv(n), hw(n);
+    std::vector<VW> hv(n);
     std::vector<int> hid(n);
     cudaStream_t s = b->stream;
     CK(cudaMemcpyAsync(hp.data(), b->B.pos, n * sizeof(double4_32a), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hv.data(), b->B.vel0, n * sizeof(float4), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hw.data(), b->B.omg0, n * sizeof(float4), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hv.data(), b->B.vw0, n * sizeof(VW), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hid.data(), b->B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s));
     dem_status st = check_fault(b);
     if (st != DEM_OK) return st;
@@ -680,8 +678,8 @@ extern "C" dem_status dem_read_state(dem_bed* b, double* pos, float* vel, float*
     for (int i = 0; i < n; ++i) {
         const int k = hid[i];
         op[3 * k] = hp[i].x; op[3 * k + 1] = hp[i].y; op[3 * k + 2] = hp[i].z;
-        ov[3 * k] = hv[i].x; ov[3 * k + 1] = hv[i].y; ov[3 * k + 2] = hv[i].z;
-        ow[3 * k] = hw[i].x; ow[3 * k + 1] = hw[i].y; ow[3 * k + 2] = hw[i].z;
+        ov[3 * k] = hv[i].v.x; ov[3 * k + 1] = hv[i].v.y; ov[3 * k + 2] = hv[i].v.z;
+        ow[3 * k] = hv[i].w.x; ow[3 * k + 1] = hv[i].w.y; ow[3 * k + 2] = hv[i].w.z;
     }
     if (pos && (st = copy_out(pos, op.data(), op.size())) != DEM_OK) return st;
     if (vel && (st = copy_out(vel, ov.data(), ov.size())) != DEM_OK) return st;

@@ -5,9 +5,8 @@
 // in the caller's arrays):
 //   bodies   pos   double4_32a (x, y, z, r)        FP64 centres, exact contact tests
 //            posr  float4  (x, y, z, r)        FP32 copy for the broad phase
-//            vel0  float4  (v, 1/m)            velocity at the start of the step
-//            omg0  float4  (w, 1/I)
-//            velA/velB, omgA/omgB              Jacobi iterates v^k (ping-pong)
+//            vw0   VW (v, 1/m | w, 1/I), 32 B     velocity at the start of the step
+//            vw[2] VW                          Jacobi iterates v^k (ping-pong)
 //   contacts one record per sphere-sphere contact, owned by one body
 //            rec   3 x float4 per contact (normal, SPOOK row data, arms, cones)
 //            lamA  float4 (p_n, p_t1, p_t2, p_r.x), lamB float2 (p_r.y, p_r.z)
@@ -27,6 +26,18 @@
 #define DEM_FIX_SCALE 17592186044416.0  // 2^44: fixed-point scale of geometry impulses [N s]
 
 enum { DEM_FLAG_CAPACITY = 1, DEM_FLAG_NONFINITE = 2 };
+
+// one body's velocity record: 32 bytes, one memory sector per gather
+struct __align__(32) VW {
+    float4 v;   // (v.x, v.y, v.z, 1/m)
+    float4 w;   // (w.x, w.y, w.z, 1/I)
+};
+
+// one incidence entry's impulse share (linear P, angular T), 32 bytes
+struct __align__(32) Imp {
+    float4 a;   // (P.x, P.y, P.z, T.x)
+    float4 b;   // (T.y, T.z, -, -)
+};
 
 struct LevelGrid {
     float ox, oy, oz;   // origin
@@ -72,10 +83,8 @@ struct DevBuf {
     // bodies
     double4_32a* pos;
     float4* posr;
-    float4* vel0;
-    float4* omg0;
-    float4* vel[2];
-    float4* omg[2];
+    VW* vw0;
+    VW* vw[2];
     int* id;
     int* lvl;
     int* prev_of;       // old slot of each slot after a re-sort
@@ -109,8 +118,7 @@ struct DevBuf {
     int2* inc;          // [2C]
     int* c_self;        // [C] slot of body a (the owner)
     int2* c_pos;        // [C] positions of the contact in a's and b's incidence lists
-    float4* impA;       // [2C] per incidence entry: impulse share (P.x, P.y, P.z, T.x)
-    float2* impB;       // [2C] (T.y, T.z)
+    Imp* imp;           // [2C] per incidence entry: impulse share of its body
     // sphere-geometry contacts (one-sided)
     int* g_key[2];      // [max_geo] primitive index, per parity
     float4* grec;       // [6 * max_geo]
@@ -125,7 +133,7 @@ struct DevBuf {
     unsigned* key_a; unsigned* key_b;
     int* val_a; int* val_b;
     int* hist;          // radix histogram [256 * blocks]
-    double4_32a* t_pos; float4* t_v; float4* t_w; int* t_id; int* t_lvl;
+    double4_32a* t_pos; VW* t_vw; int* t_id; int* t_lvl;
     // scan scratch
     int* scan_tmp;
 };

@@ -40,8 +40,7 @@ __global__ void __launch_bounds__(RS_T) k_permute_gather(SimParams P, DevBuf B) 
     if (i >= P.n) return;
     const int o = B.val_a[i];
     B.t_pos[i] = B.pos[o];
-    B.t_v[i] = B.vel0[o];
-    B.t_w[i] = B.omg0[o];
+    B.t_vw[i] = B.vw0[o];
     B.t_id[i] = B.id[o];
     B.t_lvl[i] = B.lvl[o];
     B.prev_of[i] = o;
@@ -54,8 +53,7 @@ __global__ void __launch_bounds__(RS_T) k_permute_store(SimParams P, DevBuf B) {
     const double4_32a x = B.t_pos[i];
     B.pos[i] = x;
     B.posr[i] = make_float4((float)x.x, (float)x.y, (float)x.z, (float)x.w);
-    B.vel0[i] = B.t_v[i];
-    B.omg0[i] = B.t_w[i];
+    B.vw0[i] = B.t_vw[i];
     B.id[i] = B.t_id[i];
     B.lvl[i] = B.t_lvl[i];
 }

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
     const int q = p ^ 1;
     const int prev = *B.resorted ? B.prev_of[i] : i;
     const double4_32a xa = B.pos[i];
-    const float4 va = B.vel0[i], wa = B.omg0[i];
+    const float4 va = B.vw0[i].v, wa = B.vw0[i].w;
     const int na = (B.inc_start[i + 1] - B.inc_start[i]) + (B.geo_start[p][i + 1] - B.geo_start[p][i]);
     const float ra = (float)xa.w;
 
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         const int j = B.c_other[c];
         const int key = B.c_key[p][c];
         const double4_32a xb = B.pos[j];
-        const float4 vb = B.vel0[j], wb = B.omg0[j];
+        const float4 vb = B.vw0[j].v, wb = B.vw0[j].w;
         const int nb = (B.inc_start[j + 1] - B.inc_start[j]) + (B.geo_start[p][j + 1] - B.geo_start[p][j]);
         // distance in double, overlap via (R^2 - d^2) / (R + d) to avoid cancellation
         const double dx = __dsub_rn(xa.x, xb.x), dy = __dsub_rn(xa.y, xb.y), dz = __dsub_rn(xa.z, xb.z);
@@ -239,15 +239,15 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
     const int i = gt / T, lane = gt % T;
     const bool active = i < P.n;
     const int dst = src ^ 1;
-    const float4* __restrict__ vin = UPDATE ? B.vel[src] : B.vel0;
-    const float4* __restrict__ win = UPDATE ? B.omg[src] : B.omg0;
+    const VW* __restrict__ vin = UPDATE ? B.vw[src] : B.vw0;
     const float4* __restrict__ lAin = B.lamA[src];
     const float2* __restrict__ lBin = B.lamB[src];
     float3 accL = make_float3(0.f, 0.f, 0.f), accA = make_float3(0.f, 0.f, 0.f);
     float4 vi4 = make_float4(0.f, 0.f, 0.f, 0.f), wi4 = vi4;
     if (active) {
-        vi4 = vin[i];
-        wi4 = win[i];
+        const VW me = vin[i];
+        vi4 = me.v;
+        wi4 = me.w;
         const float3 vi = f3(vi4), wi = f3(wi4);
         const int e1 = B.inc_start[i + 1];
         int e = B.inc_start[i] + lane;
@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
             if (UPDATE) {
                 const int j = ent.y;
                 const float4 r1 = B.rec[3 * (size_t)c + 1];
-                const float3 vj = f3(vin[j]), wj = f3(win[j]);
+                const VW other = vin[j];
+                const float3 vj = f3(other.v), wj = f3(other.w);
                 const float3 dv = sideb ? vj - vi : vi - vj;
                 const float3 wa = sideb ? wj : wi, wb = sideb ? wi : wj;
                 const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, dv, wa, wb, P.eps_reg);
@@ -315,14 +316,14 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
         accA = make_float3(sub_sum<T>(accA.x), sub_sum<T>(accA.y), sub_sum<T>(accA.z));
     }
     if (!active || lane != 0) return;
-    const float4 v0 = B.vel0[i], w0 = B.omg0[i];
+    const float4 v0 = B.vw0[i].v, w0 = B.vw0[i].w;
     const float gm = v0.w > 0.0f ? P.dt : 0.0f;
     const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
     const float3 v = vs + v0.w * accL;
     const float3 w = f3(w0) + w0.w * accA;
     const int out = UPDATE ? dst : 0;
-    B.vel[out][i] = make_float4(v.x, v.y, v.z, v0.w);
-    B.omg[out][i] = make_float4(w.x, w.y, w.z, w0.w);
+    B.vw[out][i].v = make_float4(v.x, v.y, v.z, v0.w);
+    B.vw[out][i].w = make_float4(w.x, w.y, w.z, w0.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -335,12 +336,12 @@ __global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = !*B.err;
     if (i < P.n && ok) {
-        const float4 v = B.vel[src][i], w = B.omg[src][i];
+        const float4 v = B.vw[src][i].v, w = B.vw[src][i].w;
         if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(w.x) && isfinite(w.y) &&
               isfinite(w.z)))
             set_flag(B.err, DEM_FLAG_NONFINITE);
-        B.vel0[i] = v;
-        B.omg0[i] = w;
+        B.vw0[i].v = v;
+        B.vw0[i].w = w;
         double4_32a x = B.pos[i];
         const double h = (double)P.dt;
         x.x = __dadd_rn(x.x, __dmul_rn(h, (double)v.x));
@@ -419,15 +420,15 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
     if (*B.err) return;
     const int dst = src ^ 1;
     const int nc = min(B.own_start[p][P.n], P.max_contacts);
-    const float4* __restrict__ vin = B.vel[src];
-    const float4* __restrict__ win = B.omg[src];
+    const VW* __restrict__ vin = B.vw[src];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         const int a = B.c_self[c], b = B.c_other[c];
         const int2 pos = B.c_pos[c];
         const float4 r0 = B.rec[3 * (size_t)c], r1 = B.rec[3 * (size_t)c + 1], r2 = B.rec[3 * (size_t)c + 2];
         const float4 l0 = B.lamA[src][c];
         const float2 l1 = B.lamB[src][c];
-        const float3 va = f3(vin[a]), wa = f3(win[a]), vb = f3(vin[b]), wb = f3(win[b]);
+        const VW A = vin[a], Bv = vin[b];
+        const float3 va = f3(A.v), wa = f3(A.w), vb = f3(Bv.v), wb = f3(Bv.w);
         const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, va - vb, wa, wb, P.eps_reg);
         const float3 n = f3(r0);
         if (LAST) {
@@ -439,10 +440,13 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
         float3 La = make_float3(0.f, 0.f, 0.f), Aa = La, Lb = La, Ab = La;
         add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
         add_impulse(n, u.t1, u.t2, r2.y, u.pn, u.pt1, u.pt2, u.pr, true, Lb, Ab);
-        B.impA[pos.x] = make_float4(La.x, La.y, La.z, Aa.x);
-        B.impB[pos.x] = make_float2(Aa.y, Aa.z);
-        B.impA[pos.y] = make_float4(Lb.x, Lb.y, Lb.z, Ab.x);
-        B.impB[pos.y] = make_float2(Ab.y, Ab.z);
+        Imp ia, ib;
+        ia.a = make_float4(La.x, La.y, La.z, Aa.x);
+        ia.b = make_float4(Aa.y, Aa.z, 0.f, 0.f);
+        ib.a = make_float4(Lb.x, Lb.y, Lb.z, Ab.x);
+        ib.b = make_float4(Ab.y, Ab.z, 0.f, 0.f);
+        B.imp[pos.x] = ia;
+        B.imp[pos.y] = ib;
     }
 }
 
@@ -457,15 +461,14 @@ __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p
     float3 accL = make_float3(0.f, 0.f, 0.f), accA = accL;
     const int e1 = B.inc_start[i + 1];
     for (int e = B.inc_start[i]; e < e1; ++e) {
-        const float4 q = B.impA[e];
-        const float2 t = B.impB[e];
-        accL = accL + f3(q);
-        accA = accA + make_float3(q.w, t.x, t.y);
+        const Imp q = B.imp[e];
+        accL = accL + f3(q.a);
+        accA = accA + make_float3(q.a.w, q.b.x, q.b.y);
     }
     const int g1 = B.geo_start[p][i + 1];
     int k = B.geo_start[p][i];
     if (k < g1) {
-        const float3 vi = f3(B.vel[src][i]), wi = f3(B.omg[src][i]);
+        const float3 vi = f3(B.vw[src][i].v), wi = f3(B.vw[src][i].w);
         for (; k < g1; ++k) {
             const float4* r = B.grec + 6 * (size_t)k;
             const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
@@ -482,13 +485,13 @@ __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p
             add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
         }
     }
-    const float4 v0 = B.vel0[i], w0 = B.omg0[i];
+    const float4 v0 = B.vw0[i].v, w0 = B.vw0[i].w;
     const float gm = v0.w > 0.0f ? P.dt : 0.0f;
     const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
     const float3 v = vs + v0.w * accL;
     const float3 w = f3(w0) + w0.w * accA;
-    B.vel[dst][i] = make_float4(v.x, v.y, v.z, v0.w);
-    B.omg[dst][i] = make_float4(w.x, w.y, w.z, w0.w);
+    B.vw[dst][i].v = make_float4(v.x, v.y, v.z, v0.w);
+    B.vw[dst][i].w = make_float4(w.x, w.y, w.z, w0.w);
 }
 
 template <typename K>

@@ -346,6 +346,7 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
 #define AL(ptr, cnt) if (st == DEM_OK) st = dalloc_n(b, &(ptr), (cnt))
     AL(B.pos, N); AL(B.posr, N); AL(B.vw0, N); AL(B.vw[0], N); AL(B.vw[1], N);
     AL(B.id, N); AL(B.lvl, N); AL(B.prev_of, N); AL(B.resorted, 1); AL(B.err, 1);
+    AL(B.lvl_lo, 3 * DEM_MAX_LEVELS); AL(B.lvl_hi, 3 * DEM_MAX_LEVELS);
     AL(B.body_cell, N); AL(B.cell_cnt, NC + 1); AL(B.cell_start, NC + 1); AL(B.cell_fill, NC + 1);
     AL(B.cell_body, N);
     AL(B.tmp_own, N * DEM_MAX_OWN); AL(B.tmp_geo, N * DEM_MAX_GEO);
@@ -458,6 +459,9 @@ static int body_pre(dem_bed* b, int p) {
     cudaMemsetAsync(B.in_cnt, 0, (N + 1) * sizeof(int), s);
     cudaMemsetAsync(B.in_fill, 0, (N + 1) * sizeof(int), s);
     cudaMemsetAsync(B.gacc, 0, 6 * std::max(P.ng, 1) * sizeof(long long), s);
+    // per-level boxes start empty: lo = huge (bytes 0x7f), hi = -huge (bytes 0x80)
+    cudaMemsetAsync(B.lvl_lo, 0x7f, 3 * DEM_MAX_LEVELS * sizeof(int), s);
+    cudaMemsetAsync(B.lvl_hi, 0x80, 3 * DEM_MAX_LEVELS * sizeof(int), s);
     if (P.n == 0) {
         cudaMemsetAsync(B.own_start[p], 0, sizeof(int), s);
         cudaMemsetAsync(B.geo_start[p], 0, sizeof(int), s);

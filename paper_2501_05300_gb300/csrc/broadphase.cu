@@ -42,12 +42,32 @@ static __device__ __forceinline__ int cell_of(const LevelGrid& g, float4 p, int&
 }
 
 __global__ void __launch_bounds__(BP_T) k_cell_count(SimParams P, DevBuf B) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
-    int cx, cy, cz;
-    int c = cell_of(P.lv[B.lvl[i]], B.posr[i], cx, cy, cz);
-    B.body_cell[i] = c;
-    atomicAdd(&B.cell_cnt[c], 1);
+    __shared__ int lo[3 * DEM_MAX_LEVELS], hi[3 * DEM_MAX_LEVELS];
+    for (int t = threadIdx.x; t < 3 * DEM_MAX_LEVELS; t += blockDim.x) {
+        lo[t] = 0x7fffffff;
+        hi[t] = (int)0x80000000;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.n) {
+        const int l = B.lvl[i];
+        const float4 p = B.posr[i];
+        int cx, cy, cz;
+        const int c = cell_of(P.lv[l], p, cx, cy, cz);
+        B.body_cell[i] = c;
+        atomicAdd(&B.cell_cnt[c], 1);
+        const float q[3] = {p.x, p.y, p.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&lo[3 * l + k], float_ord(q[k]));
+            atomicMax(&hi[3 * l + k], float_ord(q[k]));
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * P.n_levels; t += blockDim.x) {
+        if (lo[t] != 0x7fffffff) atomicMin(&B.lvl_lo[t], lo[t]);
+        if (hi[t] != (int)0x80000000) atomicMax(&B.lvl_hi[t], hi[t]);
+    }
 }
 
 __global__ void __launch_bounds__(BP_T) k_cell_fill(SimParams P, DevBuf B) {
@@ -61,9 +81,17 @@ __global__ void __launch_bounds__(BP_T) k_cell_fill(SimParams P, DevBuf B) {
 // ---------------------------------------------------------------------------
 // narrow phase
 // ---------------------------------------------------------------------------
+// PT threads per particle: the candidates of each row of cells are shared out
+// across the lanes, hits are compacted into the particle's list with a ballot
+// over the lanes, and lane 0 orders the list by the other particle's id.
+#define PT 8
 __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / PT, lane = gt % PT;
+    if (i >= P.n) return;   // whole groups leave together
+    const int grp = (threadIdx.x & 31) / PT;
+    const unsigned gmask = 0xffu << (grp * PT);
+    const unsigned below = (1u << lane) - 1u;
     const float4 pi = B.posr[i];
     const double4_32a xi = B.pos[i];
     const int li = B.lvl[i];
@@ -73,6 +101,16 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
     bool overflow = false;
     for (int l = li; l < P.n_levels; ++l) {
         const LevelGrid g = P.lv[l];
+        if (l > li) {
+            // skip a coarser level whose particles are all out of reach
+            const float reach = pi.w + g.rmax + P.tol;
+            const float q[3] = {pi.x, pi.y, pi.z};
+            bool far = false;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                far |= q[k] + reach < ord_float(B.lvl_lo[3 * l + k]) || q[k] - reach > ord_float(B.lvl_hi[3 * l + k]);
+            if (far) continue;
+        }
         int cx, cy, cz;
         cell_of(g, pi, cx, cy, cz);
         const int z0 = max(cz - 1, 0), z1 = min(cz + 1, g.nz - 1);
@@ -82,41 +120,74 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
             for (int y = y0; y <= y1; ++y) {
                 const int row = g.offset + g.nx * (y + g.ny * z);
                 const int s = B.cell_start[row + x0], e = B.cell_start[row + x1 + 1];
-                for (int k = s; k < e; ++k) {
-                    const int j = B.cell_body[k];
-                    if (j == i) continue;
-                    const float4 pj = B.posr[j];
-                    const float R = pi.w + pj.w + P.tol;
-                    const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                    if (dx * dx + dy * dy + dz * dz >= R * R) continue;
-                    const int idj = B.id[j];
-                    if (l == li && idj < idi) continue;  // same level: the lower id owns
-                    if (!exact_pair(xi, B.pos[j])) continue;
-                    if (nown < DEM_MAX_OWN) {
-                        // insertion by the other body's stable id keeps the list sorted
-                        int q = nown;
-                        while (q > 0 && own[q - 1].y > idj) { own[q] = own[q - 1]; --q; }
-                        own[q] = make_int2(j, idj);
-                        ++nown;
-                        atomicAdd(&B.in_cnt[j], 1);
-                    } else {
-                        overflow = true;
+                for (int base = s; base < e; base += PT) {
+                    const int k = base + lane;
+                    bool hit = false;
+                    int j = 0, idj = 0;
+                    if (k < e) {
+                        j = B.cell_body[k];
+                        if (j != i) {
+                            const float4 pj = B.posr[j];
+                            const float R = pi.w + pj.w + P.tol;
+                            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                            if (dx * dx + dy * dy + dz * dz < R * R) {
+                                idj = B.id[j];
+                                // same level: the lower id owns the pair
+                                if (!(l == li && idj < idi)) hit = exact_pair(xi, B.pos[j]);
+                            }
+                        }
                     }
+                    const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & 0xffu;
+                    if (hit) {
+                        const int q = nown + __popc(bal & below);
+                        if (q < DEM_MAX_OWN) {
+                            own[q] = make_int2(j, idj);
+                            atomicAdd(&B.in_cnt[j], 1);
+                        } else {
+                            overflow = true;
+                        }
+                    }
+                    nown += __popc(bal);
                 }
             }
     }
     int ngeo = 0;
     int* gl = B.tmp_geo + (size_t)i * DEM_MAX_GEO;
-    for (int gi = 0; gi < P.ng; ++gi) {
-        const GeomDev& g = B.geom[gi];
-        if (!geom_near(g, pi, P.tol)) continue;
-        GeoHit h = geom_hit(g, xi.x, xi.y, xi.z, xi.w);
-        if (!h.hit) continue;
-        if (ngeo < DEM_MAX_GEO) gl[ngeo++] = gi;
-        else overflow = true;
+    for (int base = 0; base < P.ng; base += PT) {
+        const int gi = base + lane;
+        bool hit = false;
+        if (gi < P.ng) {
+            const GeomDev& g = B.geom[gi];
+            hit = geom_near(g, pi, P.tol) && geom_hit(g, xi.x, xi.y, xi.z, xi.w).hit;
+        }
+        const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & 0xffu;
+        if (hit) {
+            const int q = ngeo + __popc(bal & below);
+            if (q < DEM_MAX_GEO) gl[q] = gi;
+            else overflow = true;
+        }
+        ngeo += __popc(bal);
     }
-    B.own_cnt[i] = nown;
-    B.geo_cnt[i] = ngeo;
+    __syncwarp(gmask);
+    if (lane == 0) {
+        nown = min(nown, DEM_MAX_OWN);
+        ngeo = min(ngeo, DEM_MAX_GEO);
+        // order the list by the other particle's stable id (primitives by index)
+        for (int a = 1; a < nown; ++a) {
+            const int2 v = own[a];
+            int q = a;
+            while (q > 0 && own[q - 1].y > v.y) { own[q] = own[q - 1]; --q; }
+            own[q] = v;
+        }
+        for (int a = 1; a < ngeo; ++a) {
+            const int v = gl[a];
+            int q = a;
+            while (q > 0 && gl[q - 1] > v) { gl[q] = gl[q - 1]; --q; }
+            gl[q] = v;
+        }
+        B.own_cnt[i] = nown;
+        B.geo_cnt[i] = ngeo;
+    }
     if (overflow) set_flag(B.err, DEM_FLAG_CAPACITY);
 }
 
@@ -203,7 +274,7 @@ int launch_cell_fill(const SimParams& P, const DevBuf& B, cudaStream_t s) {
     return 1;
 }
 int launch_pairs(const SimParams& P, const DevBuf& B, cudaStream_t s) {
-    k_pairs<<<nblk(P.n, BP_T), BP_T, 0, s>>>(P, B);
+    k_pairs<<<nblk(P.n * PT, BP_T), BP_T, 0, s>>>(P, B);
     return 1;
 }
 int launch_contacts_build(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {

@@ -91,6 +91,8 @@ struct DevBuf {
     int* resorted;      // 1 during the step that follows a re-sort
     int* err;           // latched DEM_FLAG_* bits
     // broad phase
+    int* lvl_lo;        // [3 * DEM_MAX_LEVELS] per-level bounding box of the centres,
+    int* lvl_hi;        //   floats as order-preserving ints, rebuilt every step
     int* body_cell;
     int* cell_cnt;      // [n_cells + 1]
     int* cell_start;    // [n_cells + 1]
@@ -191,3 +193,10 @@ static __device__ __forceinline__ int cell_coord(float x, float o, float inv, in
 }
 
 static __device__ __forceinline__ void set_flag(int* err, int bit) { atomicOr(err, bit); }
+
+// floats as ints whose order is the float order (for atomicMin / atomicMax)
+static __device__ __forceinline__ int float_ord(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+static __device__ __forceinline__ float ord_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }

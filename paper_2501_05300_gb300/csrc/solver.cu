@@ -450,48 +450,62 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
     }
 }
 
+// BT lanes per body: lane l adds the body's shares l, l+BT, ...; the lane sums
+// are combined by a fixed butterfly, so the result does not depend on timing.
+#define BT 4
 template <bool LAST>
 __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p, int src) {
     pdl_wait();
     pdl_trigger();
     if (*B.err) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / BT, lane = gt % BT;
+    const bool active = i < P.n;
     const int dst = src ^ 1;
     float3 accL = make_float3(0.f, 0.f, 0.f), accA = accL;
-    const int e1 = B.inc_start[i + 1];
-    for (int e = B.inc_start[i]; e < e1; ++e) {
-        const Imp q = B.imp[e];
-        accL = accL + f3(q.a);
-        accA = accA + make_float3(q.a.w, q.b.x, q.b.y);
-    }
-    const int g1 = B.geo_start[p][i + 1];
-    int k = B.geo_start[p][i];
-    if (k < g1) {
-        const float3 vi = f3(B.vw[src][i].v), wi = f3(B.vw[src][i].w);
-        for (; k < g1; ++k) {
-            const float4* r = B.grec + 6 * (size_t)k;
-            const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
-            const float4 l0 = B.glamA[src][k];
-            const float2 l1 = B.glamB[src][k];
-            const float3 n = f3(r0);
-            const Upd u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4), P.eps_reg);
-            if (LAST) {
-                write_world(B.glamW[p], k, n, u);
-            } else {
-                B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
-                B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
+    if (active) {
+        const int e1 = B.inc_start[i + 1];
+        for (int e = B.inc_start[i] + lane; e < e1; e += BT) {
+            const Imp q = B.imp[e];
+            accL = accL + f3(q.a);
+            accA = accA + make_float3(q.a.w, q.b.x, q.b.y);
+        }
+        const int g1 = B.geo_start[p][i + 1];
+        int k = B.geo_start[p][i] + lane;
+        if (k < g1) {
+            const VW me = B.vw[src][i];
+            const float3 vi = f3(me.v), wi = f3(me.w);
+            for (; k < g1; k += BT) {
+                const float4* r = B.grec + 6 * (size_t)k;
+                const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+                const float4 l0 = B.glamA[src][k];
+                const float2 l1 = B.glamB[src][k];
+                const float3 n = f3(r0);
+                const Upd u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4),
+                                             P.eps_reg);
+                if (LAST) {
+                    write_world(B.glamW[p], k, n, u);
+                } else {
+                    B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+                    B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
+                }
+                add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
             }
-            add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
         }
     }
-    const float4 v0 = B.vw0[i].v, w0 = B.vw0[i].w;
+    accL = make_float3(sub_sum<BT>(accL.x), sub_sum<BT>(accL.y), sub_sum<BT>(accL.z));
+    accA = make_float3(sub_sum<BT>(accA.x), sub_sum<BT>(accA.y), sub_sum<BT>(accA.z));
+    if (!active || lane != 0) return;
+    const VW s0 = B.vw0[i];
+    const float4 v0 = s0.v, w0 = s0.w;
     const float gm = v0.w > 0.0f ? P.dt : 0.0f;
     const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
     const float3 v = vs + v0.w * accL;
     const float3 w = f3(w0) + w0.w * accA;
-    B.vw[dst][i].v = make_float4(v.x, v.y, v.z, v0.w);
-    B.vw[dst][i].w = make_float4(w.x, w.y, w.z, w0.w);
+    VW out;
+    out.v = make_float4(v.x, v.y, v.z, v0.w);
+    out.w = make_float4(w.x, w.y, w.z, w0.w);
+    B.vw[dst][i] = out;
 }
 
 template <typename K>
@@ -552,7 +566,7 @@ int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, cudaS
     }
     // two-pass sweep: contacts (grid-stride over the capacity) then bodies
     const int cblocks = std::min(nblk(P.max_contacts, SV_T), 16 * sm_count());
-    const int bblocks = nblk(P.n, SV_T);
+    const int bblocks = nblk(P.n * BT, SV_T);
     if (last) {
         launch_pdl(k_contact_pass<true>, cblocks, s, P, B, parity, src);
         launch_pdl(k_body_pass<true>, bblocks, s, P, B, parity, src);

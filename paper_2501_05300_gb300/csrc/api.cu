@@ -353,7 +353,8 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     AL(B.own_cnt, N + 1); AL(B.in_cnt, N + 1); AL(B.geo_cnt, N + 1); AL(B.in_fill, N + 1);
     AL(B.own_start[0], N + 1); AL(B.own_start[1], N + 1); AL(B.inc_start, N + 1);
     AL(B.geo_start[0], N + 1); AL(B.geo_start[1], N + 1);
-    AL(B.c_other, C); AL(B.c_key[0], C); AL(B.c_key[1], C); AL(B.rec, 6 * C); AL(B.c_delta, C);
+    AL(B.c_other, C); AL(B.c_key[0], C); AL(B.c_key[1], C); AL(B.rec, 3 * C); AL(B.c_delta, C);
+    AL(B.lamA[0], C); AL(B.lamA[1], C); AL(B.lamB[0], C); AL(B.lamB[1], C);
     AL(B.lamW[0], 2 * C); AL(B.lamW[1], 2 * C); AL(B.inc, 2 * C);
     AL(B.c_self, C); AL(B.c_pos, C); AL(B.imp, 2 * C);
     AL(B.g_key[0], GC); AL(B.g_key[1], GC); AL(B.grec, 6 * GC); AL(B.g_delta, GC);

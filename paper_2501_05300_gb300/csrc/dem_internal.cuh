@@ -8,8 +8,8 @@
 //            vw0   VW (v, 1/m | w, 1/I), 32 B     velocity at the start of the step
 //            vw[2] VW                          Jacobi iterates v^k (ping-pong)
 //   contacts one record per sphere-sphere contact, owned by one body
-//            rec   96 B = 3 sectors: rows (normal, SPOOK data, arms, cones) and
-//                  both impulse iterates (p_n, p_t1, p_t2, p_r) of the ping-pong
+//            rec   3 x float4 per contact (normal, SPOOK row data, arms, cones)
+//            lamA  float4 (p_n, p_t1, p_t2, p_r.x), lamB float2 (p_r.y, p_r.z)
 //            lamW  2 x float4 world-frame impulses kept for the next warm start
 //   incidence per body, every contact it takes part in, ordered by the stable
 //            id of the other body: int2 (contact | side << 31, other slot)
@@ -112,8 +112,10 @@ struct DevBuf {
     // sphere-sphere contacts
     int* c_other;       // [C] slot of body b
     int* c_key[2];      // [C] stable id of body b, per parity
-    float4* rec;        // [6C] 96-byte contact records, see crec_* below
+    float4* rec;        // [3C]
     float* c_delta;     // [C] overlap, kept for read-back
+    float4* lamA[2];    // [C] iterate ping-pong
+    float2* lamB[2];
     float4* lamW[2];    // [2C] world-frame final impulses, per parity
     int2* inc;          // [2C]
     int* c_self;        // [C] slot of body a (the owner)
@@ -158,32 +160,6 @@ int launch_resort(const SimParams& P, const DevBuf& B, cudaStream_t s);
 int launch_radix_sort(unsigned* key_a, int* val_a, unsigned* key_b, int* val_b, int n, int* hist,
                       int* tmp, cudaStream_t s);
 int radix_blocks(int n);
-
-// ----------------------------------------------------------------------------
-// contact record (6 float4 = 96 B): [0] (n, 1/D_n)  [1] (b_n, Sigma_n, 1/D_t, 1/D_r)
-// [2] (arm_a, arm_b, mu_t, mu_r r_eff); impulse iterate 0 = [3] + [4].xy,
-// iterate 1 = [4].zw + [5], each as (p_n, p_t1, p_t2, p_r.x) + (p_r.y, p_r.z)
-// ----------------------------------------------------------------------------
-static __device__ __forceinline__ void crec_lam_load(const float4* cr, int buf, float4& l0, float2& l1) {
-    const float4 m = cr[4];
-    if (buf == 0) {
-        l0 = cr[3];
-        l1 = make_float2(m.x, m.y);
-    } else {
-        l0 = cr[5];
-        l1 = make_float2(m.z, m.w);
-    }
-}
-static __device__ __forceinline__ void crec_lam_store(float4* cr, int buf, float4 l0, float2 l1) {
-    float2* m = reinterpret_cast<float2*>(cr + 4);
-    if (buf == 0) {
-        cr[3] = l0;
-        m[0] = l1;
-    } else {
-        cr[5] = l0;
-        m[1] = l1;
-    }
-}
 
 // ----------------------------------------------------------------------------
 // device helpers

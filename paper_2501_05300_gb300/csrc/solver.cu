@@ -115,10 +115,9 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         const float ima = na * va.w, imb = nb * vb.w, iIa = na * wa.w, iIb = nb * wb.w;
         const float Gv = dot(n, f3(va) - f3(vb));
         const RowC rc = spook_row(P, delta, kn, Gv, ima + imb, la * la * iIa + lb * lb * iIb, iIa + iIb);
-        float4* cr = B.rec + 6 * (size_t)c;
-        cr[0] = make_float4(n.x, n.y, n.z, rc.invDn);
-        cr[1] = make_float4(rc.rhs, rc.sig, rc.invDt, rc.invDr);
-        cr[2] = make_float4(la, lb, P.mu_t, P.mu_r * dstar);
+        B.rec[3 * (size_t)c + 0] = make_float4(n.x, n.y, n.z, rc.invDn);
+        B.rec[3 * (size_t)c + 1] = make_float4(rc.rhs, rc.sig, rc.invDt, rc.invDr);
+        B.rec[3 * (size_t)c + 2] = make_float4(la, lb, P.mu_t, P.mu_r * dstar);
         B.c_delta[c] = delta;
         // warm start from the previous step's impulse of the same pair
         while (kp < pe && B.c_key[q][kp] < key) ++kp;
@@ -126,7 +125,8 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         float2 l1 = make_float2(0.f, 0.f);
         if (kp < pe && B.c_key[q][kp] == key)
             warm_project(B.lamW[q][2 * (size_t)kp], B.lamW[q][2 * (size_t)kp + 1], n, l0, l1);
-        crec_lam_store(cr, 0, l0, l1);
+        B.lamA[0][c] = l0;
+        B.lamB[0][c] = l1;
     }
 
     // sphere-geometry contacts
@@ -240,6 +240,8 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
     const bool active = i < P.n;
     const int dst = src ^ 1;
     const VW* __restrict__ vin = UPDATE ? B.vw[src] : B.vw0;
+    const float4* __restrict__ lAin = B.lamA[src];
+    const float2* __restrict__ lBin = B.lamB[src];
     float3 accL = make_float3(0.f, 0.f, 0.f), accA = make_float3(0.f, 0.f, 0.f);
     float4 vi4 = make_float4(0.f, 0.f, 0.f, 0.f), wi4 = vi4;
     if (active) {
@@ -255,15 +257,13 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
             if (e + T < e1) nxt = B.inc[e + T];   // fetch the next entry before this one's data
             const bool sideb = ent.x < 0;
             const int c = ent.x & 0x7fffffff;
-            float4* cr = B.rec + 6 * (size_t)c;
-            const float4 r0 = cr[0], r2 = cr[2];
-            float4 l0;
-            float2 l1;
-            crec_lam_load(cr, src, l0, l1);
+            const float4 r0 = B.rec[3 * (size_t)c], r2 = B.rec[3 * (size_t)c + 2];
+            const float4 l0 = lAin[c];
+            const float2 l1 = lBin[c];
             const float3 n = f3(r0);
             if (UPDATE) {
                 const int j = ent.y;
-                const float4 r1 = cr[1];
+                const float4 r1 = B.rec[3 * (size_t)c + 1];
                 const VW other = vin[j];
                 const float3 vj = f3(other.v), wj = f3(other.w);
                 const float3 dv = sideb ? vj - vi : vi - vj;
@@ -273,7 +273,8 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
                     if (LAST) {
                         write_world(B.lamW[p], c, n, u);
                     } else {
-                        crec_lam_store(cr, dst, make_float4(u.pn, u.pt1, u.pt2, u.pr.x), make_float2(u.pr.y, u.pr.z));
+                        B.lamA[dst][c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+                        B.lamB[dst][c] = make_float2(u.pr.y, u.pr.z);
                     }
                 }
                 add_impulse(n, u.t1, u.t2, sideb ? r2.y : r2.x, u.pn, u.pt1, u.pt2, u.pr, sideb, accL, accA);
@@ -423,11 +424,9 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         const int a = B.c_self[c], b = B.c_other[c];
         const int2 pos = B.c_pos[c];
-        float4* cr = B.rec + 6 * (size_t)c;
-        const float4 r0 = cr[0], r1 = cr[1], r2 = cr[2];
-        float4 l0;
-        float2 l1;
-        crec_lam_load(cr, src, l0, l1);
+        const float4 r0 = B.rec[3 * (size_t)c], r1 = B.rec[3 * (size_t)c + 1], r2 = B.rec[3 * (size_t)c + 2];
+        const float4 l0 = B.lamA[src][c];
+        const float2 l1 = B.lamB[src][c];
         const VW A = vin[a], Bv = vin[b];
         const float3 va = f3(A.v), wa = f3(A.w), vb = f3(Bv.v), wb = f3(Bv.w);
         const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, va - vb, wa, wb, P.eps_reg);
@@ -435,7 +434,8 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
         if (LAST) {
             write_world(B.lamW[p], c, n, u);
         } else {
-            crec_lam_store(cr, dst, make_float4(u.pn, u.pt1, u.pt2, u.pr.x), make_float2(u.pr.y, u.pr.z));
+            B.lamA[dst][c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+            B.lamB[dst][c] = make_float2(u.pr.y, u.pr.z);
         }
         float3 La = make_float3(0.f, 0.f, 0.f), Aa = La, Lb = La, Ab = La;
         add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
 
 // BT lanes per body: lane l adds the body's shares l, l+BT, ...; the lane sums
 // are combined by a fixed butterfly, so the result does not depend on timing.
-#define BT 1
+#define BT 4
 template <bool LAST>
 __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p, int src) {
     pdl_wait();

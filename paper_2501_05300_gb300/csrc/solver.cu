@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
 
 // BT lanes per body: lane l adds the body's shares l, l+BT, ...; the lane sums
 // are combined by a fixed butterfly, so the result does not depend on timing.
-#define BT 4
+#define BT 1
 template <bool LAST>
 __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p, int src) {
     pdl_wait();

@@ -113,12 +113,34 @@ typedef struct dem_info {
     int64_t contact_capacity;
     int32_t kernels_per_step;   /* kernel launches of one plain (non-resort) step */
     int32_t kernels_per_resort; /* extra launches of a re-sort */
+    int32_t n_beds;             /* beds advanced together (dem_create_batch) */
+    int32_t lanes;              /* current sweep layout (see dem_bed_desc.lanes) */
+    int32_t resort_every;       /* current Morton re-sort period */
 } dem_info;
 
 /* Create a bed from particles, materials and geometry.
  * stream: a cudaStream_t (NULL = the library creates a non-blocking stream).
  * Synchronous: returns when the bed is ready.  On failure *out is NULL. */
 dem_status dem_create_bed(const dem_bed_desc* desc, void* stream, dem_bed** out);
+
+/* Create one object advancing nbeds independent beds together, every step in
+ * one graph launch: many small beds, like the paper's 36 refinement variants
+ * (Sec. 3.3, Table 2), fill the GPU together where one alone would not.
+ * descs[k] describes bed k exactly as for dem_create_bed; the solver and
+ * material settings (dt, e_H, damp_steps, E, nu, mu_t, mu_r, gravity, kn_scale,
+ * eps_reg, delta_floor) must be equal across beds, n_it (Eq. 8) may differ.
+ * Particles of bed k get the stable ids after those of beds 0..k-1, and its
+ * primitives the indices after theirs (all dem_read_* calls use these global
+ * numbers).  Beds never interact, even where they overlap in space.  Allocator,
+ * re-sort period, level ratio and lanes are taken from descs[0]. */
+dem_status dem_create_batch(const dem_bed_desc* descs, int32_t nbeds, void* stream, dem_bed** out);
+
+/* Autotuner: times trial_steps steps (after one untimed step) of every sweep
+ * layout (lanes 0, 1, 2, 4, 8), keeps the fastest, then times re-sort periods
+ * 5, 10, 20, 50 and keeps the fastest.  The bed advances by those steps: call it
+ * in place of warm-up steps.  Choices are returned through lanes_out and
+ * resort_out (either may be NULL) and stay in effect.  Synchronises. */
+dem_status dem_autotune(dem_bed* bed, int32_t trial_steps, int32_t* lanes_out, int32_t* resort_out);
 
 /* Enqueue nsteps time steps (detection, SPOOK rows, N_it Jacobi sweeps,
  * integration; Sec. 2.2) on the bed's stream.  Asynchronous. */

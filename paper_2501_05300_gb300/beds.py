@@ -184,6 +184,79 @@ def refined_layers(top_r=2.5e-3, top_thickness=0.02, growth=2.0, n_coarser=3, de
     return list(reversed(tops))
 
 
+def graded_layers(top_r, top_thickness, growth, cap_ratio=8.0, depth=0.25):
+    """Layers (bottom up) of a bed refined from the top: the top layer has
+    radius top_r and thickness eta d_0 = top_thickness; below it every layer's
+    radius grows by `growth` (d_n = r d_{n-1}) and its thickness is eta d_n
+    (Sec. 2.1), the radius capped at cap_ratio * top_r; the capped size fills
+    the rest of the depth."""
+    eta = top_thickness / (2 * top_r)
+    cap = cap_ratio * top_r
+    out, r, z = [], top_r, 0.0
+    while True:
+        t = eta * 2 * r
+        if r >= cap * (1 - 1e-9) or z + t >= depth - 1e-12:
+            out.append((r, depth - z))
+            break
+        out.append((r, t))
+        z += t
+        r = min(r * growth, cap)
+    return list(reversed(out))
+
+
+def natural_density(layers, spread=0.1, phi=0.636):
+    """Particles per square metre of footprint of a layer list."""
+    tot = 0.0
+    for r, t in layers:
+        m3 = r ** 3 * ((1 + spread) ** 4 - (1 - spread) ** 4) / (8 * spread)
+        tot += t * phi / (4.0 / 3.0 * math.pi * m3)
+    return tot
+
+
+BATCH_DEPTHS = (0.01, 0.02, 0.03, 0.04, 0.06, 0.08)
+BATCH_GROWTHS = (1.25, 1.5, 1.75, 2.0, 2.5, 3.0)
+
+
+def batch_specs(n_min=20_000, n_max=500_000, depth=0.25, r0=2.5e-3):
+    """The 6 x 6 grid of refinement depth x radius growth: for each bed its
+    layers, the footprint side that gives its particle count, and N_it from
+    Eqs. 8 and 10.  Counts are log-spaced from n_min to n_max in the order of
+    the beds' natural densities."""
+    combos = [(dd, g, graded_layers(r0, dd, g, depth=depth)) for dd in BATCH_DEPTHS for g in BATCH_GROWTHS]
+    dens = [natural_density(l) for _, _, l in combos]
+    order = sorted(range(len(combos)), key=lambda k: dens[k])
+    counts = np.geomspace(n_min, n_max, len(combos))
+    out = [None] * len(combos)
+    for rank, k in enumerate(order):
+        dd, g, layers = combos[k]
+        side = math.sqrt(counts[rank] / dens[k])
+        eta = dd / (2 * r0)
+        d_min, d_max = 2 * r0, 2 * max(r for r, _ in layers)
+        zmax = sum(t for r, t in layers if r < max(r for r, _ in layers))
+        from .rules import n_iterations, network_length_refined, network_length_uniform
+        if d_max > d_min * (1 + 1e-9):
+            nd = network_length_refined(eta, d_min, d_max, g, depth, zmax)
+        else:
+            nd = network_length_uniform(depth, d_min)
+        out[k] = dict(depth=dd, growth=g, layers=layers, side=side, target=int(counts[rank]),
+                      n_it=n_iterations(nd, 0.02))
+    return out
+
+
+def batch_bed(spec, seed, phi=0.636):
+    """One bed of the batch grid on its square footprint, with bin walls and a
+    0.1 m disc plate above the centre."""
+    side = spec["side"]
+    x, r = layered_bed(side, side, spec["layers"], spread=0.1, phi=phi, seed=seed)
+    geoms = open_box_walls(side, side)
+    zs = float((x[:, 2] + r).max())
+    geoms.append(GeomSpec(CYLINDER, (side / 2, side / 2, zs + 0.005 + 0.001), he=(0.05, 0.0, 0.005),
+                          mu_t=0.5, mu_r=0.02))
+    mat = Material(rho=2600.0, mu_t=0.5, mu_r=0.02)
+    return Bed(x, r, geoms, mat, name=f"batch bed depth {spec['depth']} growth {spec['growth']}",
+               plate=len(geoms) - 1, plate_parts=(len(geoms) - 1,), box=(side, side, 0.25))
+
+
 def refined_sinkage_bed(lx=0.89, ly=0.89, depth=0.25, seed=2503, phi=0.636):
     """Refined bed for plate sinkage: r = 2.5 mm in the top 2 cm, doubling per
     layer below (5, 10, 20 mm; max size ratio 8), 10% radius spread.  A

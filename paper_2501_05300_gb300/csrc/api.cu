@@ -52,6 +52,8 @@ struct dem_bed {
     void* actx = nullptr;
     std::vector<void*> allocs;
     int n_geom = 0;
+    int nbeds = 1;
+    std::vector<LevelGrid> levels;   // host copy of the level table
     std::vector<double> z_ref;  // particle surface under each primitive at creation
     // graphs: [parity][pre, jac, post]
     cudaGraphExec_t g[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -146,29 +148,57 @@ static void surface_refs(int n, const double* pos, int ps, const double* rad, in
     }
 }
 
-extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_bed** out) {
-    g_err.clear();
-    if (!out) return fail(DEM_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (!d) return fail(DEM_ERR_ARG, "desc is NULL");
-    const int n = d->n;
-    if (n < 0) return fail(DEM_ERR_ARG, "n = %d < 0", n);
-    if (n > 0 && (!d->pos || !d->radius)) return fail(DEM_ERR_ARG, "pos and radius are required");
-    if (d->n_geom < 0 || d->n_geom > DEM_MAX_GEOM)
-        return fail(DEM_ERR_ARG, "n_geom = %d outside [0, %d]", d->n_geom, DEM_MAX_GEOM);
-    if (d->n_geom > 0 && !d->geom) return fail(DEM_ERR_ARG, "geom is NULL");
+// Shared settings of all beds in one object (one SimParams).
+static bool same_settings(const dem_bed_desc& a, const dem_bed_desc& b) {
+    return a.E == b.E && a.nu == b.nu && a.mu_t == b.mu_t && a.mu_r == b.mu_r && a.e_H == b.e_H &&
+           a.damp_steps == b.damp_steps && a.dt == b.dt && a.gravity[0] == b.gravity[0] &&
+           a.gravity[1] == b.gravity[1] && a.gravity[2] == b.gravity[2] && a.kn_scale == b.kn_scale &&
+           a.eps_reg == b.eps_reg && a.delta_floor == b.delta_floor;
+}
+
+static dem_status check_desc(const dem_bed_desc* d, int k) {
+    if (d->n < 0) return fail(DEM_ERR_ARG, "bed %d: n = %d < 0", k, d->n);
+    if (d->n > 0 && (!d->pos || !d->radius)) return fail(DEM_ERR_ARG, "bed %d: pos and radius are required", k);
+    if (d->n_geom < 0) return fail(DEM_ERR_ARG, "bed %d: n_geom < 0", k);
+    if (d->n_geom > 0 && !d->geom) return fail(DEM_ERR_ARG, "bed %d: geom is NULL", k);
     if (!(d->dt > 0.f)) return fail(DEM_ERR_ARG, "dt must be > 0");
-    if (d->n_it < 0) return fail(DEM_ERR_ARG, "n_it < 0");
+    if (d->n_it < 0) return fail(DEM_ERR_ARG, "bed %d: n_it < 0", k);
     if (!(d->E > 0.f) || !(d->nu > -1.f && d->nu < 0.5f)) return fail(DEM_ERR_ARG, "bad E or nu");
     if (!(d->e_H >= 1.f)) return fail(DEM_ERR_ARG, "e_H must be >= 1");
-    if (!(d->rho > 0.f) && !(d->inv_mass && d->inv_inertia)) return fail(DEM_ERR_ARG, "rho must be > 0");
+    if (!(d->rho > 0.f) && !(d->inv_mass && d->inv_inertia)) return fail(DEM_ERR_ARG, "bed %d: rho must be > 0", k);
     if (d->damp_steps < 0.f || d->mu_t < 0.f || d->mu_r < 0.f || d->eps_reg < 0.f)
         return fail(DEM_ERR_ARG, "negative damping, friction or regularisation");
     for (int g = 0; g < d->n_geom; ++g) {
         const dem_geom& G = d->geom[g];
-        if (G.type < 0 || G.type > 2) return fail(DEM_ERR_ARG, "geom %d: bad type %d", g, G.type);
-        if (!(G.E > 0.f) || G.mu_t < 0.f || G.mu_r < 0.f) return fail(DEM_ERR_ARG, "geom %d: bad material", g);
+        if (G.type < 0 || G.type > 2) return fail(DEM_ERR_ARG, "bed %d geom %d: bad type %d", k, g, G.type);
+        if (!(G.E > 0.f) || G.mu_t < 0.f || G.mu_r < 0.f) return fail(DEM_ERR_ARG, "bed %d geom %d: bad material", k, g);
     }
+    return DEM_OK;
+}
+
+// One object for one or many beds.  Bed k's particles get the stable ids that
+// follow those of beds 0..k-1, its primitives the indices that follow theirs.
+// Every bed has its own grid levels (one per radius band), so particles of
+// different beds never meet even where the beds overlap in space.
+static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream, dem_bed** out) {
+    g_err.clear();
+    if (!out) return fail(DEM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!descs || nbeds < 1) return fail(DEM_ERR_ARG, "desc is NULL or no beds");
+    int64_t n64 = 0, ng64 = 0, cap_sum = 0;
+    for (int k = 0; k < nbeds; ++k) {
+        dem_status st = check_desc(&descs[k], k);
+        if (st != DEM_OK) return st;
+        if (!same_settings(descs[0], descs[k]))
+            return fail(DEM_ERR_ARG, "bed %d: solver and material settings differ from bed 0", k);
+        n64 += descs[k].n;
+        ng64 += descs[k].n_geom;
+        cap_sum += descs[k].contact_capacity > 0 ? descs[k].contact_capacity : 8LL * descs[k].n;
+    }
+    if (n64 > (int64_t)0x7fffffff / 8) return fail(DEM_ERR_ARG, "too many particles");
+    if (ng64 > DEM_MAX_GEOM) return fail(DEM_ERR_ARG, "%lld primitives exceed %d", (long long)ng64, DEM_MAX_GEOM);
+    const dem_bed_desc* d = &descs[0];
+    const int n = (int)n64;
 
     dem_bed* b = new dem_bed();
     cudaGetDevice(&b->dev);
@@ -189,152 +219,223 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
         return fail(DEM_ERR_ARG, "alloc and free_fn must be given together");
     }
     b->resort_every = d->resort_every > 0 ? d->resort_every : 20;
-    b->n_geom = d->n_geom;
+    b->n_geom = (int)ng64;
+    b->nbeds = nbeds;
 
     // host copies of the inputs (they may live on the device)
     std::vector<double> pos(3 * (size_t)n);
     std::vector<float> rad(n), vel(3 * (size_t)n, 0.f), omg(3 * (size_t)n, 0.f), im(n), iI(n);
+    std::vector<int> bed_of(n);
+    std::vector<dem_geom> geoms;
+    std::vector<int> geom_bed;
     auto fetch = [&](void* dst, const void* src, size_t bytes) -> bool {
         return cudaMemcpy(dst, src, bytes, cudaMemcpyDefault) == cudaSuccess;
     };
-    if (n > 0) {
-        bool ok = fetch(pos.data(), d->pos, pos.size() * 8) && fetch(rad.data(), d->radius, rad.size() * 4);
-        if (d->vel) ok = ok && fetch(vel.data(), d->vel, vel.size() * 4);
-        if (d->omega) ok = ok && fetch(omg.data(), d->omega, omg.size() * 4);
-        if (d->inv_mass) ok = ok && fetch(im.data(), d->inv_mass, im.size() * 4);
-        if (d->inv_inertia) ok = ok && fetch(iI.data(), d->inv_inertia, iI.size() * 4);
-        if (!ok) {
-            release(b);
-            return fail(DEM_ERR_ARG, "could not read the input arrays");
-        }
-    }
-    double rmin = 1e300, rmaxg = 0.0;
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int i = 0; i < n; ++i) {
-        if (!(rad[i] > 0.f) || !std::isfinite(rad[i])) {
-            release(b);
-            return fail(DEM_ERR_ARG, "radius[%d] = %g is not positive", i, (double)rad[i]);
-        }
-        for (int k = 0; k < 3; ++k) {
-            if (!std::isfinite(pos[3 * i + k])) {
-                release(b);
-                return fail(DEM_ERR_ARG, "pos[%d] is not finite", i);
-            }
-            lo[k] = std::min(lo[k], pos[3 * i + k]);
-            hi[k] = std::max(hi[k], pos[3 * i + k]);
-        }
-        rmin = std::min(rmin, (double)rad[i]);
-        rmaxg = std::max(rmaxg, (double)rad[i]);
-        const double m = (double)d->rho * 4.0 / 3.0 * M_PI * rad[i] * rad[i] * rad[i];
-        if (!d->inv_mass) im[i] = (float)(1.0 / m);
-        if (!d->inv_inertia) iI[i] = (float)(1.0 / (0.4 * m * rad[i] * rad[i]));
-    }
-    if (n == 0) { rmin = rmaxg = 1e-3; for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = 0; } }
-
-    // radius bands: level k holds rmin * ratio^k <= r < rmin * ratio^(k+1)
-    const double ratio = d->level_ratio > 1.f ? d->level_ratio : 2.0;
-    std::vector<int> lvl(n, 0);
-    int lmax = 0;
-    for (int i = 0; i < n; ++i) {
-        int k = 0;
-        double edge = rmin * ratio;
-        while (k < DEM_MAX_LEVELS - 1 && (double)rad[i] >= edge) { ++k; edge *= ratio; }
-        lvl[i] = k;
-        lmax = std::max(lmax, k);
-    }
-    // drop empty levels
-    std::vector<int> remap(lmax + 1, -1);
-    std::vector<double> lev_rmax;
     {
-        std::vector<int> used(lmax + 1, 0);
-        for (int i = 0; i < n; ++i) used[lvl[i]] = 1;
-        if (n == 0) used[0] = 1;
-        for (int k = 0; k <= lmax; ++k)
-            if (used[k]) { remap[k] = (int)lev_rmax.size(); lev_rmax.push_back(0.0); }
-        for (int i = 0; i < n; ++i) {
-            lvl[i] = remap[lvl[i]];
-            lev_rmax[lvl[i]] = std::max(lev_rmax[lvl[i]], (double)rad[i]);
+        size_t o = 0;
+        for (int k = 0; k < nbeds; ++k) {
+            const dem_bed_desc& dk = descs[k];
+            const size_t m = dk.n;
+            bool ok = true;
+            if (m > 0) {
+                ok = fetch(&pos[3 * o], dk.pos, 3 * m * 8) && fetch(&rad[o], dk.radius, m * 4);
+                if (dk.vel) ok = ok && fetch(&vel[3 * o], dk.vel, 3 * m * 4);
+                if (dk.omega) ok = ok && fetch(&omg[3 * o], dk.omega, 3 * m * 4);
+                if (dk.inv_mass) ok = ok && fetch(&im[o], dk.inv_mass, m * 4);
+                if (dk.inv_inertia) ok = ok && fetch(&iI[o], dk.inv_inertia, m * 4);
+            }
+            if (!ok) {
+                release(b);
+                return fail(DEM_ERR_ARG, "bed %d: could not read the input arrays", k);
+            }
+            for (size_t i = 0; i < m; ++i) {
+                bed_of[o + i] = k;
+                if (!(rad[o + i] > 0.f) || !std::isfinite(rad[o + i])) {
+                    release(b);
+                    return fail(DEM_ERR_ARG, "bed %d: radius[%zu] = %g is not positive", k, i, (double)rad[o + i]);
+                }
+                for (int q = 0; q < 3; ++q)
+                    if (!std::isfinite(pos[3 * (o + i) + q])) {
+                        release(b);
+                        return fail(DEM_ERR_ARG, "bed %d: pos[%zu] is not finite", k, i);
+                    }
+                const double r = rad[o + i];
+                const double mass = (double)dk.rho * 4.0 / 3.0 * M_PI * r * r * r;
+                if (!dk.inv_mass) im[o + i] = (float)(1.0 / mass);
+                if (!dk.inv_inertia) iI[o + i] = (float)(1.0 / (0.4 * mass * r * r));
+            }
+            for (int g = 0; g < dk.n_geom; ++g) {
+                geoms.push_back(dk.geom[g]);
+                geom_bed.push_back(k);
+            }
+            o += m;
         }
-        if (n == 0) lev_rmax[0] = rmaxg;
     }
-    const int L = (int)lev_rmax.size();
 
     SimParams& P = b->P;
+    double rmin_all = 1e300, rmax_all = 0.0, absmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        rmin_all = std::min(rmin_all, (double)rad[i]);
+        rmax_all = std::max(rmax_all, (double)rad[i]);
+        for (int q = 0; q < 3; ++q) absmax = std::max(absmax, std::fabs(pos[3 * i + q]));
+    }
+    if (n == 0) rmin_all = rmax_all = 1e-3;
+    // FP32 rounding of the copies: <= 2^-24 |x| per coordinate (margin included)
+    P.tol = (float)(4.0 * std::ldexp(absmax * 1.25 + 8.0 * rmax_all, -23) + 8.0 * std::ldexp(2.0 * rmax_all, -24));
+
+    // grid levels: per bed, one per radius band rmin_bed * ratio^k <= r < rmin_bed * ratio^(k+1)
+    const double ratio = d->level_ratio > 1.f ? d->level_ratio : 2.0;
+    std::vector<int> lvl(n, 0);
+    std::vector<LevelGrid> levels;
+    int max_nit = 0;
+    int64_t total_cells = 0;
+    {
+        size_t o = 0;
+        int g0 = 0;
+        for (int k = 0; k < nbeds; ++k) {
+            const dem_bed_desc& dk = descs[k];
+            const int m = dk.n;
+            max_nit = std::max(max_nit, dk.n_it);
+            double rmin = 1e300;
+            for (int i = 0; i < m; ++i) rmin = std::min(rmin, (double)rad[o + i]);
+            std::vector<int> band(m, 0);
+            int bmax = 0;
+            for (int i = 0; i < m; ++i) {
+                int q = 0;
+                double edge = rmin * ratio;
+                while (q < 15 && (double)rad[o + i] >= edge) { ++q; edge *= ratio; }
+                band[i] = q;
+                bmax = std::max(bmax, q);
+            }
+            // the bed's levels: non-empty bands in increasing size
+            const int first = (int)levels.size();
+            std::vector<int> remap(bmax + 1, -1);
+            std::vector<char> used(bmax + 1, 0);
+            for (int i = 0; i < m; ++i) used[band[i]] = 1;
+            if (m == 0) used[0] = 1;
+            for (int q = 0; q <= bmax; ++q)
+                if (used[q]) {
+                    remap[q] = (int)levels.size();
+                    LevelGrid g;
+                    memset(&g, 0, sizeof g);
+                    g.bed = k;
+                    g.nit = dk.n_it;
+                    levels.push_back(g);
+                }
+            if ((int)levels.size() > DEM_MAX_LEVELS) {
+                release(b);
+                return fail(DEM_ERR_ARG, "more than %d grid levels over all beds", DEM_MAX_LEVELS);
+            }
+            const int last = (int)levels.size();
+            // bounding box and largest radius of every level
+            std::vector<double> lo(3 * (last - first), 1e300), hi(3 * (last - first), -1e300), rmx(last - first, 0.0);
+            for (int i = 0; i < m; ++i) {
+                const int l = remap[band[i]];
+                lvl[o + i] = l;
+                const int j = l - first;
+                rmx[j] = std::max(rmx[j], (double)rad[o + i]);
+                for (int q = 0; q < 3; ++q) {
+                    lo[3 * j + q] = std::min(lo[3 * j + q], pos[3 * (o + i) + q]);
+                    hi[3 * j + q] = std::max(hi[3 * j + q], pos[3 * (o + i) + q]);
+                }
+            }
+            for (int l = first; l < last; ++l) {
+                LevelGrid& g = levels[l];
+                const int j = l - first;
+                if (m == 0) {
+                    rmx[j] = 1e-3;
+                    for (int q = 0; q < 3; ++q) { lo[3 * j + q] = 0; hi[3 * j + q] = 0; }
+                }
+                double ext = 0.0;
+                for (int q = 0; q < 3; ++q) ext = std::max(ext, hi[3 * j + q] - lo[3 * j + q]);
+                // the grid covers the level's particles plus a margin; particles
+                // that leave it are clamped into the boundary cells (still exact)
+                const double margin = std::max(8.0 * rmx[j], 0.1 * ext);
+                double cell = 2.0 * rmx[j] * (1.0 + 1e-4) + 2.0 * P.tol;
+                int dims[3];
+                for (;;) {
+                    int64_t c = 1;
+                    for (int q = 0; q < 3; ++q) {
+                        dims[q] = std::max(1, (int)std::ceil((hi[3 * j + q] - lo[3 * j + q] + 2 * margin) / cell));
+                        c *= dims[q];
+                    }
+                    if (c <= (int64_t)(32 << 20)) break;
+                    cell *= 1.25;   // cap the cell count; larger cells stay correct
+                }
+                g.ox = (float)(lo[3 * j] - margin);
+                g.oy = (float)(lo[3 * j + 1] - margin);
+                g.oz = (float)(lo[3 * j + 2] - margin);
+                g.cell = (float)cell;
+                g.inv_cell = (float)(1.0 / cell);
+                g.nx = dims[0]; g.ny = dims[1]; g.nz = dims[2];
+                g.offset = (int)total_cells;
+                g.rmax = (float)rmx[j];
+                g.lend = last;
+                g.g0 = g0;
+                g.g1 = g0 + dk.n_geom;
+                total_cells += (int64_t)dims[0] * dims[1] * dims[2];
+            }
+            g0 += dk.n_geom;
+            o += m;
+        }
+    }
+    if (total_cells > (int64_t)(256 << 20)) {
+        release(b);
+        return fail(DEM_ERR_ARG, "broad-phase grids need %lld cells", (long long)total_cells);
+    }
+    const int L = (int)levels.size();
     P.n = n;
-    P.ng = d->n_geom;
+    P.ng = (int)ng64;
     P.n_levels = L;
-    P.n_it = d->n_it;
+    P.n_cells = (int)total_cells;
+    P.n_it = max_nit;
     P.dt = d->dt;
     P.inv_dt = 1.0f / d->dt;
     P.e_H = d->e_H;
     P.kn_scale = d->kn_scale > 0.f ? d->kn_scale : 1.0f;
     P.eps_reg = d->eps_reg;
-    P.delta_floor = d->delta_floor > 0.f ? d->delta_floor : (float)(1e-6 * 2.0 * rmin);
+    P.delta_floor = d->delta_floor > 0.f ? d->delta_floor : (float)(1e-6 * 2.0 * rmin_all);
     P.ups = 1.0f / (1.0f + 4.0f * d->damp_steps);
     P.Estar_ss = (float)estar(d->E, d->nu, d->E, d->nu);
     P.mu_t = d->mu_t;
     P.mu_r = d->mu_r;
     P.gx = d->gravity[0]; P.gy = d->gravity[1]; P.gz = d->gravity[2];
-    int64_t cap = d->contact_capacity > 0 ? d->contact_capacity : 8LL * n + 1024;
+    int64_t cap = cap_sum + 1024;
     if (cap > (int64_t)0x3fffffff) cap = 0x3fffffff;
     P.max_contacts = (int)cap;
     P.max_geo = 2 * n + 1024;
     P.lanes = d->lanes;   // 0: two-pass sweep; 1, 2, 4, 8: one kernel, that many threads per body
     if (P.lanes != 0 && P.lanes != 1 && P.lanes != 2 && P.lanes != 4 && P.lanes != 8) {
         release(b);
-        return fail(DEM_ERR_ARG, "lanes = %d is not 1, 2, 4 or 8", d->lanes);
+        return fail(DEM_ERR_ARG, "lanes = %d is not 0, 1, 2, 4 or 8", d->lanes);
     }
+    b->levels = levels;
+    P.nit_uniform = 1;
+    for (int k = 1; k < nbeds; ++k) P.nit_uniform &= descs[k].n_it == descs[0].n_it;
 
-    // grids over the particle bounding box plus a margin
-    double ext = 0.0, absmax = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        ext = std::max(ext, hi[k] - lo[k]);
-        absmax = std::max(absmax, std::max(std::fabs(lo[k]), std::fabs(hi[k])));
-    }
-    const double margin = std::max(4.0 * rmaxg, 0.05 * ext);
-    // FP32 rounding of the copies: <= 2^-24 |x| per coordinate
-    P.tol = (float)(4.0 * std::ldexp(absmax + margin, -23) + 8.0 * std::ldexp(2.0 * rmaxg, -24));
-    int64_t total_cells = 0;
-    for (int l = 0; l < L; ++l) {
-        LevelGrid& g = P.lv[l];
-        double cell = 2.0 * lev_rmax[l] * (1.0 + 1e-4) + 2.0 * P.tol;
-        int dims[3];
-        for (;;) {
-            int64_t c = 1;
-            for (int k = 0; k < 3; ++k) {
-                dims[k] = std::max(1, (int)std::ceil((hi[k] - lo[k] + 2 * margin) / cell));
-                c *= dims[k];
-            }
-            if (c <= (int64_t)(48 << 20)) break;
-            cell *= 1.25;   // cap the cell count; larger cells stay correct
-        }
-        g.ox = (float)(lo[0] - margin);
-        g.oy = (float)(lo[1] - margin);
-        g.oz = (float)(lo[2] - margin);
-        g.cell = (float)cell;
-        g.inv_cell = (float)(1.0 / cell);
-        g.nx = dims[0]; g.ny = dims[1]; g.nz = dims[2];
-        g.offset = (int)total_cells;
-        g.rmax = (float)lev_rmax[l];
-        total_cells += (int64_t)dims[0] * dims[1] * dims[2];
-    }
-    if (total_cells > (int64_t)(200 << 20)) {
-        release(b);
-        return fail(DEM_ERR_ARG, "broad-phase grids need %lld cells", (long long)total_cells);
-    }
-    P.n_cells = (int)total_cells;
-
-    // sinkage references: highest particle top under each primitive's footprint
+    // sinkage references: highest particle top under each primitive's footprint (its own bed)
     {
-        std::vector<int> types(P.ng);
-        std::vector<double> gc(3 * (size_t)P.ng), gR(9 * (size_t)P.ng), ghe(3 * (size_t)P.ng);
-        for (int g = 0; g < P.ng; ++g) {
-            types[g] = d->geom[g].type;
-            for (int k = 0; k < 3; ++k) { gc[3 * g + k] = d->geom[g].c[k]; ghe[3 * g + k] = d->geom[g].he[k]; }
-            for (int k = 0; k < 9; ++k) gR[9 * g + k] = d->geom[g].R[k];
+        b->z_ref.assign(P.ng, 0.0);
+        size_t o = 0;
+        int g0 = 0;
+        for (int k = 0; k < nbeds; ++k) {
+            const dem_bed_desc& dk = descs[k];
+            const int ngk = dk.n_geom;
+            std::vector<int> types(ngk);
+            std::vector<double> gc(3 * (size_t)ngk), gR(9 * (size_t)ngk), ghe(3 * (size_t)ngk);
+            for (int g = 0; g < ngk; ++g) {
+                types[g] = dk.geom[g].type;
+                for (int q = 0; q < 3; ++q) { gc[3 * g + q] = dk.geom[g].c[q]; ghe[3 * g + q] = dk.geom[g].he[q]; }
+                for (int q = 0; q < 9; ++q) gR[9 * g + q] = dk.geom[g].R[q];
+            }
+            std::vector<double> rr(rad.begin() + o, rad.begin() + o + dk.n);
+            std::vector<double> zr;
+            surface_refs(dk.n, pos.data() + 3 * o, 3, rr.data(), 1, ngk, types.data(), gc.data(), gR.data(),
+                         ghe.data(), zr);
+            for (int g = 0; g < ngk; ++g) b->z_ref[g0 + g] = zr[g];
+            g0 += ngk;
+            o += dk.n;
         }
-        std::vector<double> rr(rad.begin(), rad.end());
-        surface_refs(n, pos.data(), 3, rr.data(), 1, P.ng, types.data(), gc.data(), gR.data(), ghe.data(), b->z_ref);
     }
 
     // ---- device memory ----
@@ -344,9 +445,10 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     const int nbr = radix_blocks(n);
     dem_status st = DEM_OK;
 #define AL(ptr, cnt) if (st == DEM_OK) st = dalloc_n(b, &(ptr), (cnt))
+    AL(B.lv, (size_t)L);
     AL(B.pos, N); AL(B.posr, N); AL(B.vw0, N); AL(B.vw[0], N); AL(B.vw[1], N);
     AL(B.id, N); AL(B.lvl, N); AL(B.prev_of, N); AL(B.resorted, 1); AL(B.err, 1);
-    AL(B.lvl_lo, 3 * DEM_MAX_LEVELS); AL(B.lvl_hi, 3 * DEM_MAX_LEVELS);
+    AL(B.lvl_lo, 3 * (size_t)L); AL(B.lvl_hi, 3 * (size_t)L);
     AL(B.body_cell, N); AL(B.cell_cnt, NC + 1); AL(B.cell_start, NC + 1); AL(B.cell_fill, NC + 1);
     AL(B.cell_body, N);
     AL(B.tmp_own, N * DEM_MAX_OWN); AL(B.tmp_geo, N * DEM_MAX_GEO);
@@ -388,7 +490,7 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     }
     std::vector<GeomDev> hg(std::max(P.ng, 1));
     for (int g = 0; g < P.ng; ++g) {
-        const dem_geom& G = d->geom[g];
+        const dem_geom& G = geoms[g];
         GeomDev& o = hg[g];
         memset(&o, 0, sizeof o);
         for (int k = 0; k < 3; ++k) { o.c[k] = G.c[k]; o.he[k] = G.he[k]; o.v[k] = G.v[k]; o.w[k] = G.w[k]; }
@@ -401,6 +503,7 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
                                                  : std::sqrt(G.he[0] * G.he[0] + G.he[2] * G.he[2])) * 1.0001f;
     }
     cudaStream_t s = b->stream;
+    CK(cudaMemcpyAsync(B.lv, levels.data(), L * sizeof(LevelGrid), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.pos, hp.data(), N * sizeof(double4_32a), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.posr, hr.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.vw0, hv.data(), N * sizeof(VW), cudaMemcpyHostToDevice, s));
@@ -426,6 +529,14 @@ extern "C" dem_status dem_create_bed(const dem_bed_desc* d, void* stream, dem_be
     }
     *out = b;
     return DEM_OK;
+}
+
+extern "C" dem_status dem_create_bed(const dem_bed_desc* desc, void* stream, dem_bed** out) {
+    return create_impl(desc, 1, stream, out);
+}
+
+extern "C" dem_status dem_create_batch(const dem_bed_desc* descs, int32_t nbeds, void* stream, dem_bed** out) {
+    return create_impl(descs, nbeds, stream, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -460,8 +571,8 @@ static int body_pre(dem_bed* b, int p) {
     cudaMemsetAsync(B.in_fill, 0, (N + 1) * sizeof(int), s);
     cudaMemsetAsync(B.gacc, 0, 6 * std::max(P.ng, 1) * sizeof(long long), s);
     // per-level boxes start empty: lo = huge (bytes 0x7f), hi = -huge (bytes 0x80)
-    cudaMemsetAsync(B.lvl_lo, 0x7f, 3 * DEM_MAX_LEVELS * sizeof(int), s);
-    cudaMemsetAsync(B.lvl_hi, 0x80, 3 * DEM_MAX_LEVELS * sizeof(int), s);
+    cudaMemsetAsync(B.lvl_lo, 0x7f, 3 * (size_t)P.n_levels * sizeof(int), s);
+    cudaMemsetAsync(B.lvl_hi, 0x80, 3 * (size_t)P.n_levels * sizeof(int), s);
     if (P.n == 0) {
         cudaMemsetAsync(B.own_start[p], 0, sizeof(int), s);
         cudaMemsetAsync(B.geo_start[p], 0, sizeof(int), s);
@@ -772,6 +883,9 @@ extern "C" dem_status dem_get_info(dem_bed* b, dem_info* out) {
     out->contact_capacity = b->P.max_contacts;
     out->kernels_per_step = b->k_step;
     out->kernels_per_resort = b->k_resort;
+    out->n_beds = b->nbeds;
+    out->lanes = b->P.lanes;
+    out->resort_every = b->resort_every;
     if (b->steps > 0 && b->P.n > 0) {
         const int p = (int)((b->steps - 1) & 1);
         int a = 0, g = 0;
@@ -835,7 +949,9 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
         k_rescale_warm<<<256, 256, 0, b->stream>>>(b->B, p, P.n, scale, P.max_contacts, P.max_geo);
         CK(cudaGetLastError());
     }
-    P.n_it = d->n_it;
+    P.n_it = d->n_it;   // every bed now takes n_it sweeps
+    P.nit_uniform = 1;
+    for (LevelGrid& g : b->levels) g.nit = d->n_it;
     P.dt = d->dt;
     P.inv_dt = 1.0f / d->dt;
     P.e_H = d->e_H;
@@ -846,6 +962,8 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
     P.mu_r = d->mu_r;
     P.gx = d->gravity[0]; P.gy = d->gravity[1]; P.gz = d->gravity[2];
     P.lanes = lanes;
+    CK(cudaMemcpyAsync(b->B.lv, b->levels.data(), b->levels.size() * sizeof(LevelGrid), cudaMemcpyHostToDevice,
+                       b->stream));
     CK(cudaStreamSynchronize(b->stream));
     // the test phase starts here: re-take the surface under every primitive
     if (P.n > 0 && P.ng > 0) {
@@ -868,6 +986,73 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
             if (b->g[p][k]) { cudaGraphExecDestroy(b->g[p][k]); b->g[p][k] = nullptr; }
     if (b->g_resort) { cudaGraphExecDestroy(b->g_resort); b->g_resort = nullptr; }
     return build_graphs(b);
+}
+
+static dem_status rebuild_graphs(dem_bed* b) {
+    CK(cudaStreamSynchronize(b->stream));
+    for (int p = 0; p < 2; ++p)
+        for (int k = 0; k < 3; ++k)
+            if (b->g[p][k]) { cudaGraphExecDestroy(b->g[p][k]); b->g[p][k] = nullptr; }
+    if (b->g_resort) { cudaGraphExecDestroy(b->g_resort); b->g_resort = nullptr; }
+    return build_graphs(b);
+}
+
+// time `steps` steps of the current configuration on the bed's stream [ms]
+static dem_status time_steps(dem_bed* b, int steps, float* ms) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const bool was = b->timing;
+    b->timing = false;
+    CK(cudaEventRecord(e0, b->stream));
+    dem_status st = dem_step(b, steps);
+    CK(cudaEventRecord(e1, b->stream));
+    CK(cudaEventSynchronize(e1));
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->timing = was;
+    return st;
+}
+
+extern "C" dem_status dem_autotune(dem_bed* b, int32_t trial_steps, int32_t* lanes_out, int32_t* resort_out) {
+    g_err.clear();
+    if (!b) return fail(DEM_ERR_ARG, "bed is NULL");
+    if (trial_steps < 1) return fail(DEM_ERR_ARG, "trial_steps < 1");
+    if (b->faulted) return fail(DEM_ERR_STATE, "the bed holds a latched device fault");
+    CK(cudaSetDevice(b->dev));
+    dem_status st;
+    // every candidate first runs one untimed step, then trial_steps timed ones
+    const int lane_opts[5] = {0, 1, 2, 4, 8};
+    int best_lanes = b->P.lanes;
+    float best = 1e30f;
+    for (int k = 0; k < 5; ++k) {
+        b->P.lanes = lane_opts[k];
+        if ((st = rebuild_graphs(b)) != DEM_OK) return st;
+        if ((st = dem_step(b, 1)) != DEM_OK) return st;
+        float ms = 0;
+        if ((st = time_steps(b, trial_steps, &ms)) != DEM_OK) return st;
+        if ((st = check_fault(b)) != DEM_OK) return st;
+        if (ms < best) { best = ms; best_lanes = lane_opts[k]; }
+    }
+    b->P.lanes = best_lanes;
+    if ((st = rebuild_graphs(b)) != DEM_OK) return st;
+    // re-sort period: a re-sort costs a few kernels, a stale order costs locality
+    const int resort_opts[4] = {5, 10, 20, 50};
+    int best_resort = b->resort_every;
+    best = 1e30f;
+    for (int k = 0; k < 4; ++k) {
+        b->resort_every = resort_opts[k];
+        const int n = std::max(trial_steps, 2 * resort_opts[k]);
+        float ms = 0;
+        if ((st = time_steps(b, n, &ms)) != DEM_OK) return st;
+        if ((st = check_fault(b)) != DEM_OK) return st;
+        if (ms / n < best) { best = ms / n; best_resort = resort_opts[k]; }
+    }
+    b->resort_every = best_resort;
+    if (lanes_out) *lanes_out = best_lanes;
+    if (resort_out) *resort_out = best_resort;
+    return DEM_OK;
 }
 
 extern "C" dem_status dem_destroy_bed(dem_bed* b) {

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(BP_T) k_cell_count(SimParams P, DevBuf B) {
         const int l = B.lvl[i];
         const float4 p = B.posr[i];
         int cx, cy, cz;
-        const int c = cell_of(P.lv[l], p, cx, cy, cz);
+        const int c = cell_of(B.lv[l], p, cx, cy, cz);
         B.body_cell[i] = c;
         atomicAdd(&B.cell_cnt[c], 1);
         const float q[3] = {p.x, p.y, p.z};
@@ -99,8 +99,9 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
     int2* own = B.tmp_own + (size_t)i * DEM_MAX_OWN;
     int nown = 0;
     bool overflow = false;
-    for (int l = li; l < P.n_levels; ++l) {
-        const LevelGrid g = P.lv[l];
+    const int lend = B.lv[li].lend, gbeg = B.lv[li].g0, gend = B.lv[li].g1;
+    for (int l = li; l < lend; ++l) {
+        const LevelGrid g = B.lv[l];
         if (l > li) {
             // skip a coarser level whose particles are all out of reach
             const float reach = pi.w + g.rmax + P.tol;
@@ -153,10 +154,10 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
     }
     int ngeo = 0;
     int* gl = B.tmp_geo + (size_t)i * DEM_MAX_GEO;
-    for (int base = 0; base < P.ng; base += PT) {
+    for (int base = gbeg; base < gend; base += PT) {
         const int gi = base + lane;
         bool hit = false;
-        if (gi < P.ng) {
+        if (gi < gend) {
             const GeomDev& g = B.geom[gi];
             hit = geom_near(g, pi, P.tol) && geom_hit(g, xi.x, xi.y, xi.z, xi.w).hit;
         }

@@ -19,8 +19,8 @@
 
 #include "dem.h"
 
-#define DEM_MAX_LEVELS 8
-#define DEM_MAX_GEOM 32
+#define DEM_MAX_LEVELS 256  // grid levels over all beds (radius bands x beds)
+#define DEM_MAX_GEOM 512    // kinematic primitives over all beds
 #define DEM_MAX_OWN 32   // sphere-sphere contacts one body may own per step
 #define DEM_MAX_GEO 8    // sphere-geometry contacts per body per step
 #define DEM_FIX_SCALE 17592186044416.0  // 2^44: fixed-point scale of geometry impulses [N s]
@@ -39,6 +39,7 @@ struct __align__(32) Imp {
     float4 b;   // (T.y, T.z, -, -)
 };
 
+// One grid level: the particles of one radius band of one bed.
 struct LevelGrid {
     float ox, oy, oz;   // origin
     float inv_cell;     // 1 / cell size
@@ -46,6 +47,11 @@ struct LevelGrid {
     int offset;         // first global cell index of the level
     float rmax;         // largest radius of the level
     float cell;
+    int bed;            // the bed the level belongs to
+    int lend;           // one past the bed's last (coarsest) level
+    int g0, g1;         // the bed's primitives
+    int nit;            // the bed's Jacobi sweeps per step
+    int pad[3];
 };
 
 struct GeomDev {
@@ -73,13 +79,14 @@ struct SimParams {
     float mu_t, mu_r;
     float gx, gy, gz;
     float tol;          // FP32 broad-phase tolerance [m], covers FP32 rounding of positions
-    int lanes;          // threads per body in the Jacobi sweep (1, 2, 4 or 8)
-    LevelGrid lv[DEM_MAX_LEVELS];
+    int lanes;          // sweep layout: 0 two-pass, else threads per body in one kernel
+    int nit_uniform;    // 1 when every bed takes n_it sweeps
 };
 
 // Device pointers of one bed.  The two warm-start generations (parity of the
 // step number) are indexed [0] / [1].
 struct DevBuf {
+    LevelGrid* lv;      // [n_levels] grid levels (bed-major, fine to coarse)
     // bodies
     double4_32a* pos;
     float4* posr;
@@ -91,7 +98,7 @@ struct DevBuf {
     int* resorted;      // 1 during the step that follows a re-sort
     int* err;           // latched DEM_FLAG_* bits
     // broad phase
-    int* lvl_lo;        // [3 * DEM_MAX_LEVELS] per-level bounding box of the centres,
+    int* lvl_lo;        // [3 * n_levels] per-level bounding box of the centres,
     int* lvl_hi;        //   floats as order-preserving ints, rebuilt every step
     int* body_cell;
     int* cell_cnt;      // [n_cells + 1]
@@ -193,6 +200,11 @@ static __device__ __forceinline__ int cell_coord(float x, float o, float inv, in
 }
 
 static __device__ __forceinline__ void set_flag(int* err, int bit) { atomicOr(err, bit); }
+
+// Jacobi sweeps per step of the bed of body i
+static __device__ __forceinline__ int body_nit(const SimParams& P, const DevBuf& B, int i) {
+    return P.nit_uniform ? P.n_it : B.lv[B.lvl[i]].nit;
+}
 
 // floats as ints whose order is the float order (for atomicMin / atomicMax)
 static __device__ __forceinline__ int float_ord(float f) {

@@ -7,9 +7,9 @@
 
 #define RS_T 256
 
-// spread the low 9 bits of v to every third bit
+// spread the low 8 bits of v to every third bit
 static __device__ __forceinline__ unsigned spread3(unsigned v) {
-    v &= 0x1ffu;
+    v &= 0xffu;
     v = (v | (v << 16)) & 0x030000ffu;
     v = (v | (v << 8)) & 0x0300f00fu;
     v = (v | (v << 4)) & 0x030c30c3u;
@@ -21,17 +21,17 @@ __global__ void __launch_bounds__(RS_T) k_morton(SimParams P, DevBuf B) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const int l = B.lvl[i];
-    const LevelGrid& g = P.lv[l];
+    const LevelGrid g = B.lv[l];
     const float4 p = B.posr[i];
     unsigned cx = cell_coord(p.x, g.ox, g.inv_cell, g.nx);
     unsigned cy = cell_coord(p.y, g.oy, g.inv_cell, g.ny);
     unsigned cz = cell_coord(p.z, g.oz, g.inv_cell, g.nz);
-    // keep 9 bits per axis
+    // keep 8 bits per axis below the level index
     int m = max(g.nx, max(g.ny, g.nz));
     int sh = 0;
-    while ((m >> sh) > 512) ++sh;
+    while ((m >> sh) > 256) ++sh;
     cx >>= sh; cy >>= sh; cz >>= sh;
-    B.key_a[i] = ((unsigned)l << 27) | (spread3(cz) << 2) | (spread3(cy) << 1) | spread3(cx);
+    B.key_a[i] = ((unsigned)l << 24) | (spread3(cz) << 2) | (spread3(cy) << 1) | spread3(cx);
     B.val_a[i] = i;
 }
 

@@ -232,23 +232,26 @@ static __device__ __forceinline__ float sub_sum(float v) {
     return v;
 }
 
-template <int T, bool UPDATE, bool LAST>
-__global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, int src, int write_final) {
+template <int T, bool UPDATE>
+__global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, int it) {
     if (*B.err) return;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gt / T, lane = gt % T;
-    const bool active = i < P.n;
+    bool active = i < P.n;
+    // sweep `it` reads iterate it&1 and writes the other; the warm-start body
+    // pass (UPDATE = false) reads iterate 0 and writes velocities 0
+    const int src = UPDATE ? (it & 1) : 0;
     const int dst = src ^ 1;
+    const int nit = active ? body_nit(P, B, i) : 0;
+    if (UPDATE) active = active && it < nit;              // this bed has finished its sweeps
+    const bool last = UPDATE ? it == nit - 1 : nit == 0;  // write the final impulses
     const VW* __restrict__ vin = UPDATE ? B.vw[src] : B.vw0;
     const float4* __restrict__ lAin = B.lamA[src];
     const float2* __restrict__ lBin = B.lamB[src];
     float3 accL = make_float3(0.f, 0.f, 0.f), accA = make_float3(0.f, 0.f, 0.f);
-    float4 vi4 = make_float4(0.f, 0.f, 0.f, 0.f), wi4 = vi4;
     if (active) {
         const VW me = vin[i];
-        vi4 = me.v;
-        wi4 = me.w;
-        const float3 vi = f3(vi4), wi = f3(wi4);
+        const float3 vi = f3(me.v), wi = f3(me.w);
         const int e1 = B.inc_start[i + 1];
         int e = B.inc_start[i] + lane;
         int2 nxt = e < e1 ? B.inc[e] : make_int2(0, 0);
@@ -261,6 +264,7 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
             const float4 l0 = lAin[c];
             const float2 l1 = lBin[c];
             const float3 n = f3(r0);
+            Upd u;
             if (UPDATE) {
                 const int j = ent.y;
                 const float4 r1 = B.rec[3 * (size_t)c + 1];
@@ -268,23 +272,17 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
                 const float3 vj = f3(other.v), wj = f3(other.w);
                 const float3 dv = sideb ? vj - vi : vi - vj;
                 const float3 wa = sideb ? wj : wi, wb = sideb ? wi : wj;
-                const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, dv, wa, wb, P.eps_reg);
-                if (!sideb) {
-                    if (LAST) {
-                        write_world(B.lamW[p], c, n, u);
-                    } else {
-                        B.lamA[dst][c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
-                        B.lamB[dst][c] = make_float2(u.pr.y, u.pr.z);
-                    }
+                u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, dv, wa, wb, P.eps_reg);
+                if (!sideb && !last) {
+                    B.lamA[dst][c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+                    B.lamB[dst][c] = make_float2(u.pr.y, u.pr.z);
                 }
-                add_impulse(n, u.t1, u.t2, sideb ? r2.y : r2.x, u.pn, u.pt1, u.pt2, u.pr, sideb, accL, accA);
             } else {
-                Upd u;
                 tangent_basis(n, u.t1, u.t2);
                 u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
-                if (write_final && !sideb) write_world(B.lamW[p], c, n, u);
-                add_impulse(n, u.t1, u.t2, sideb ? r2.y : r2.x, u.pn, u.pt1, u.pt2, u.pr, sideb, accL, accA);
             }
+            if (last && !sideb) write_world(B.lamW[p], c, n, u);
+            add_impulse(n, u.t1, u.t2, sideb ? r2.y : r2.x, u.pn, u.pt1, u.pt2, u.pr, sideb, accL, accA);
         }
         const int g1 = B.geo_start[p][i + 1];
         for (int k = B.geo_start[p][i] + lane; k < g1; k += T) {
@@ -297,17 +295,15 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
             if (UPDATE) {
                 const float4 r1 = r[1], r3 = r[3], r4 = r[4];
                 u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4), P.eps_reg);
-                if (LAST) {
-                    write_world(B.glamW[p], k, n, u);
-                } else {
+                if (!last) {
                     B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
                     B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
                 }
             } else {
                 tangent_basis(n, u.t1, u.t2);
                 u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
-                if (write_final) write_world(B.glamW[p], k, n, u);
             }
+            if (last) write_world(B.glamW[p], k, n, u);
             add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
         }
     }
@@ -316,26 +312,32 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
         accA = make_float3(sub_sum<T>(accA.x), sub_sum<T>(accA.y), sub_sum<T>(accA.z));
     }
     if (!active || lane != 0) return;
-    const float4 v0 = B.vw0[i].v, w0 = B.vw0[i].w;
+    const VW s0 = B.vw0[i];
+    const float4 v0 = s0.v, w0 = s0.w;
     const float gm = v0.w > 0.0f ? P.dt : 0.0f;
     const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
     const float3 v = vs + v0.w * accL;
     const float3 w = f3(w0) + w0.w * accA;
-    const int out = UPDATE ? dst : 0;
-    B.vw[out][i].v = make_float4(v.x, v.y, v.z, v0.w);
-    B.vw[out][i].w = make_float4(w.x, w.y, w.z, w0.w);
+    VW o;
+    o.v = make_float4(v.x, v.y, v.z, v0.w);
+    o.w = make_float4(w.x, w.y, w.z, w0.w);
+    B.vw[UPDATE ? dst : 0][i] = o;
 }
 
 // ---------------------------------------------------------------------------
 // x += dt v (SPOOK position update), geometry forces, kinematic geometry
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p, int src) {
-    __shared__ long long sacc[6 * DEM_MAX_GEOM];
-    for (int t = threadIdx.x; t < 6 * P.ng; t += blockDim.x) sacc[t] = 0;
+#define SMEM_GEOM 64   // up to this many primitives the block sums impulses in shared memory
+__global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p) {
+    __shared__ long long sacc[6 * SMEM_GEOM];
+    const bool small = P.ng <= SMEM_GEOM;
+    if (small)
+        for (int t = threadIdx.x; t < 6 * P.ng; t += blockDim.x) sacc[t] = 0;
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = !*B.err;
     if (i < P.n && ok) {
+        const int src = body_nit(P, B, i) & 1;   // the bed's final iterate
         const float4 v = B.vw[src][i].v, w = B.vw[src][i].w;
         if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(w.x) && isfinite(w.y) &&
               isfinite(w.z)))
@@ -359,14 +361,16 @@ __global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p
             const float3 Tg = cross(f3(r5), Pg) - make_float3(W1.x, W1.y, W1.z);
             const float vals[6] = {Pg.x, Pg.y, Pg.z, Tg.x, Tg.y, Tg.z};
 #pragma unroll
-            for (int c = 0; c < 6; ++c)
-                atomicAdd((unsigned long long*)&sacc[6 * g + c],
-                          (unsigned long long)__double2ll_rn((double)vals[c] * DEM_FIX_SCALE));
+            for (int c = 0; c < 6; ++c) {
+                const unsigned long long q = (unsigned long long)__double2ll_rn((double)vals[c] * DEM_FIX_SCALE);
+                atomicAdd(small ? (unsigned long long*)&sacc[6 * g + c] : (unsigned long long*)&B.gacc[6 * g + c], q);
+            }
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 6 * P.ng; t += blockDim.x)
-        if (sacc[t] != 0) atomicAdd((unsigned long long*)&B.gacc[t], (unsigned long long)sacc[t]);
+    if (small)
+        for (int t = threadIdx.x; t < 6 * P.ng; t += blockDim.x)
+            if (sacc[t] != 0) atomicAdd((unsigned long long*)&B.gacc[t], (unsigned long long)sacc[t]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // kinematic primitives: translate with v, rotate with w (Rodrigues)
         const double h = (double)P.dt;
@@ -413,16 +417,18 @@ int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s
 static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 static __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
-template <bool LAST>
-__global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, int p, int src) {
+__global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, int p, int it) {
     pdl_wait();
     pdl_trigger();
     if (*B.err) return;
-    const int dst = src ^ 1;
+    const int src = it & 1, dst = src ^ 1;
     const int nc = min(B.own_start[p][P.n], P.max_contacts);
     const VW* __restrict__ vin = B.vw[src];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         const int a = B.c_self[c], b = B.c_other[c];
+        const int nit = body_nit(P, B, a);
+        if (it >= nit) continue;              // this bed has finished its sweeps
+        const bool last = it == nit - 1;
         const int2 pos = B.c_pos[c];
         const float4 r0 = B.rec[3 * (size_t)c], r1 = B.rec[3 * (size_t)c + 1], r2 = B.rec[3 * (size_t)c + 2];
         const float4 l0 = B.lamA[src][c];
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
         const float3 va = f3(A.v), wa = f3(A.w), vb = f3(Bv.v), wb = f3(Bv.w);
         const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, va - vb, wa, wb, P.eps_reg);
         const float3 n = f3(r0);
-        if (LAST) {
+        if (last) {
             write_world(B.lamW[p], c, n, u);
         } else {
             B.lamA[dst][c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
@@ -453,15 +459,16 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
 // BT lanes per body: lane l adds the body's shares l, l+BT, ...; the lane sums
 // are combined by a fixed butterfly, so the result does not depend on timing.
 #define BT 1
-template <bool LAST>
-__global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p, int src) {
+__global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p, int it) {
     pdl_wait();
     pdl_trigger();
     if (*B.err) return;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gt / BT, lane = gt % BT;
-    const bool active = i < P.n;
-    const int dst = src ^ 1;
+    const int nit = i < P.n ? body_nit(P, B, i) : 0;
+    const bool active = i < P.n && it < nit;
+    const bool last = it == nit - 1;
+    const int src = it & 1, dst = src ^ 1;
     float3 accL = make_float3(0.f, 0.f, 0.f), accA = accL;
     if (active) {
         const int e1 = B.inc_start[i + 1];
@@ -483,7 +490,7 @@ __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p
                 const float3 n = f3(r0);
                 const Upd u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4),
                                              P.eps_reg);
-                if (LAST) {
+                if (last) {
                     write_world(B.glamW[p], k, n, u);
                 } else {
                     B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
@@ -509,7 +516,7 @@ __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p
 }
 
 template <typename K>
-static void launch_pdl(K kernel, int blocks, cudaStream_t s, const SimParams& P, const DevBuf& B, int p, int src) {
+static void launch_pdl(K kernel, int blocks, cudaStream_t s, const SimParams& P, const DevBuf& B, int p, int it) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(SV_T);
@@ -519,7 +526,7 @@ static void launch_pdl(K kernel, int blocks, cudaStream_t s, const SimParams& P,
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, P, B, p, src);
+    cudaLaunchKernelEx(&cfg, kernel, P, B, p, it);
 }
 
 static int sm_count() {
@@ -534,49 +541,42 @@ static int sm_count() {
 }
 
 template <int T>
-static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int src, bool update, bool last,
-                         int write_final, cudaStream_t s) {
+static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int it, bool update, cudaStream_t s) {
     const int blocks = nblk(P.n * T, SV_T);
-    if (!update) k_sweep<T, false, false><<<blocks, SV_T, 0, s>>>(P, B, parity, 0, write_final);
-    else if (last) k_sweep<T, true, true><<<blocks, SV_T, 0, s>>>(P, B, parity, src, 0);
-    else k_sweep<T, true, false><<<blocks, SV_T, 0, s>>>(P, B, parity, src, 0);
+    if (update) k_sweep<T, true><<<blocks, SV_T, 0, s>>>(P, B, parity, it);
+    else k_sweep<T, false><<<blocks, SV_T, 0, s>>>(P, B, parity, -1);
 }
 
-static void sweep_dispatch(const SimParams& P, const DevBuf& B, int parity, int src, bool update, bool last,
-                           int write_final, cudaStream_t s) {
+static void sweep_dispatch(const SimParams& P, const DevBuf& B, int parity, int it, bool update, cudaStream_t s) {
     switch (P.lanes > 0 ? P.lanes : 2) {
-        case 1: sweep_launch<1>(P, B, parity, src, update, last, write_final, s); break;
-        case 2: sweep_launch<2>(P, B, parity, src, update, last, write_final, s); break;
-        case 8: sweep_launch<8>(P, B, parity, src, update, last, write_final, s); break;
-        default: sweep_launch<4>(P, B, parity, src, update, last, write_final, s); break;
+        case 1: sweep_launch<1>(P, B, parity, it, update, s); break;
+        case 2: sweep_launch<2>(P, B, parity, it, update, s); break;
+        case 8: sweep_launch<8>(P, B, parity, it, update, s); break;
+        default: sweep_launch<4>(P, B, parity, it, update, s); break;
     }
 }
 
 int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
-    // v^0 goes to vel[0]; with no sweeps the warm start is also the final impulse
-    sweep_dispatch(P, B, parity, 0, false, false, P.n_it == 0 ? 1 : 0, s);
+    // v^0 from the warm-start impulses into velocities 0; a bed with no sweeps
+    // keeps its warm start as the final impulse
+    sweep_dispatch(P, B, parity, -1, false, s);
     return 1;
 }
+
 int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s) {
-    const int src = it & 1;
-    const bool last = it == P.n_it - 1;
     if (P.lanes > 0) {   // single-kernel sweep, T threads per body
-        sweep_dispatch(P, B, parity, src, true, last, 0, s);
+        sweep_dispatch(P, B, parity, it, true, s);
         return 1;
     }
-    // two-pass sweep: contacts (grid-stride over the capacity) then bodies
+    // two-pass sweep: contacts (grid-stride) then bodies
     const int cblocks = std::min(nblk(P.max_contacts, SV_T), 16 * sm_count());
     const int bblocks = nblk(P.n * BT, SV_T);
-    if (last) {
-        launch_pdl(k_contact_pass<true>, cblocks, s, P, B, parity, src);
-        launch_pdl(k_body_pass<true>, bblocks, s, P, B, parity, src);
-    } else {
-        launch_pdl(k_contact_pass<false>, cblocks, s, P, B, parity, src);
-        launch_pdl(k_body_pass<false>, bblocks, s, P, B, parity, src);
-    }
+    launch_pdl(k_contact_pass, cblocks, s, P, B, parity, it);
+    launch_pdl(k_body_pass, bblocks, s, P, B, parity, it);
     return 2;
 }
+
 int launch_integrate(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
-    k_integrate<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity, P.n_it & 1);
+    k_integrate<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity);
     return 1;
 }

@@ -24,7 +24,7 @@ STATUS = {0: "DEM_OK", 1: "DEM_ERR_ARG", 2: "DEM_ERR_CUDA", 3: "DEM_ERR_CAPACITY
 PLANE, BOX, CYLINDER = 0, 1, 2
 
 # every entry point declared in include/dem.h
-EXPORTS = ("dem_create_bed", "dem_step", "dem_apply_plate_velocity", "dem_read_forces",
+EXPORTS = ("dem_create_bed", "dem_create_batch", "dem_autotune", "dem_step", "dem_apply_plate_velocity", "dem_read_forces",
            "dem_read_state", "dem_read_contacts", "dem_read_geom", "dem_sync", "dem_get_info",
            "dem_set_timing", "dem_read_timing", "dem_set_params", "dem_destroy_bed",
            "dem_detect_contacts_noalloc", "dem_last_error")
@@ -63,7 +63,8 @@ class dem_info(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_levels", C.c_int32), ("n_cells", C.c_int64),
                 ("contacts", C.c_int64), ("geom_contacts", C.c_int64), ("steps", C.c_int64),
                 ("contact_capacity", C.c_int64), ("kernels_per_step", C.c_int32),
-                ("kernels_per_resort", C.c_int32)]
+                ("kernels_per_resort", C.c_int32), ("n_beds", C.c_int32), ("lanes", C.c_int32),
+                ("resort_every", C.c_int32)]
 
 
 _lib = None
@@ -96,6 +97,8 @@ def load(build: bool = True):
     vp, i32, i64, dp, fp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.c_void_p
     sigs = {
         "dem_create_bed": (i32, [C.POINTER(dem_bed_desc), vp, C.POINTER(vp)]),
+        "dem_create_batch": (i32, [C.POINTER(dem_bed_desc), i32, vp, C.POINTER(vp)]),
+        "dem_autotune": (i32, [vp, i32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "dem_step": (i32, [vp, i32]),
         "dem_apply_plate_velocity": (i32, [vp, i32, dp, dp]),
         "dem_read_forces": (i32, [vp, i32, dp, dp, dp]),
@@ -179,66 +182,89 @@ class _TorchAllocator:
         self.torch.cuda.caching_allocator_delete(ptr)
 
 
+def _make_desc(x, r, keep, *, v=None, w=None, geoms=(), rho=2600.0, E=1e9, nu=0.15, mu_t=0.5,
+               mu_r=0.02, e_H=1.25, damp_steps=4.5, dt=1e-5, n_it=100, gravity=(0.0, 0.0, -9.81),
+               kn_scale=1.0, eps_reg=1e-6, delta_floor=0.0, inv_mass=None, inv_inertia=None,
+               contact_capacity=0, resort_every=0, level_ratio=0.0, lanes=0):
+    """A dem_bed_desc for one bed; arrays that must outlive the call go to keep."""
+    x = _input(x, np.float64, (-1, 3))
+    r = _input(r, np.float32, (-1,))
+    n = int(r.shape[0])
+    if int(x.shape[0]) != n:
+        raise ValueError("x and r disagree in length")
+    keep += [x, r]
+    d = dem_bed_desc()
+    d.n = n
+    d.pos, d.radius = _ptr(x), _ptr(r)
+    for name, arr, shape in (("vel", v, (n, 3)), ("omega", w, (n, 3)), ("inv_mass", inv_mass, (n,)),
+                             ("inv_inertia", inv_inertia, (n,))):
+        if arr is not None:
+            a = _input(arr, np.float32, shape)
+            keep.append(a)
+            setattr(d, name, _ptr(a))
+    d.rho, d.E, d.nu, d.mu_t, d.mu_r = rho, E, nu, mu_t, mu_r
+    d.e_H, d.damp_steps, d.dt, d.n_it = e_H, damp_steps, dt, int(n_it)
+    d.gravity = (C.c_float * 3)(*map(float, gravity))
+    d.kn_scale, d.eps_reg, d.delta_floor = kn_scale, eps_reg, delta_floor
+    geoms = list(geoms)
+    garr = (dem_geom * max(1, len(geoms)))(*[geom_struct(g) for g in geoms])
+    keep.append(garr)
+    d.n_geom = len(geoms)
+    d.geom = C.cast(garr, C.POINTER(dem_geom))
+    d.contact_capacity = int(contact_capacity)
+    d.resort_every = int(resort_every)
+    d.level_ratio = float(level_ratio)
+    d.lanes = int(lanes)
+    return d, n, geoms
+
+
 class Bed:
     """A bed of spheres advanced by the CUDA library.
 
     x: float64 [N,3] centres, r: float32 [N] radii, geoms: objects with the
     GeomSpec fields.  Material and solver parameters follow dem_bed_desc."""
 
-    def __init__(self, x, r, *, v=None, w=None, geoms=(), rho=2600.0, E=1e9, nu=0.15, mu_t=0.5,
-                 mu_r=0.02, e_H=1.25, damp_steps=4.5, dt=1e-5, n_it=100, gravity=(0.0, 0.0, -9.81),
-                 kn_scale=1.0, eps_reg=1e-6, delta_floor=0.0, inv_mass=None, inv_inertia=None,
-                 contact_capacity=0, resort_every=0, level_ratio=0.0, lanes=0, stream=None,
-                 use_torch=True):
+    def __init__(self, x, r, *, stream=None, use_torch=True, **kw):
         self.lib = load()
         self._handle = C.c_void_p()
-        x = _input(x, np.float64, (-1, 3))
-        r = _input(r, np.float32, (-1,))
-        n = int(r.shape[0])
-        if int(x.shape[0]) != n:
-            raise ValueError("x and r disagree in length")
-        keep = [x, r]
-        d = dem_bed_desc()
-        d.n = n
-        d.pos, d.radius = _ptr(x), _ptr(r)
-        for name, arr, shape in (("vel", v, (n, 3)), ("omega", w, (n, 3)), ("inv_mass", inv_mass, (n,)),
-                                 ("inv_inertia", inv_inertia, (n,))):
-            if arr is not None:
-                a = _input(arr, np.float32, shape)
-                keep.append(a)
-                setattr(d, name, _ptr(a))
-        d.rho, d.E, d.nu, d.mu_t, d.mu_r = rho, E, nu, mu_t, mu_r
-        d.e_H, d.damp_steps, d.dt, d.n_it = e_H, damp_steps, dt, int(n_it)
-        d.gravity = (C.c_float * 3)(*map(float, gravity))
-        d.kn_scale, d.eps_reg, d.delta_floor = kn_scale, eps_reg, delta_floor
-        self.geoms = list(geoms)
-        garr = (dem_geom * max(1, len(self.geoms)))(*[geom_struct(g) for g in self.geoms])
-        d.n_geom = len(self.geoms)
-        d.geom = C.cast(garr, C.POINTER(dem_geom))
-        d.contact_capacity = int(contact_capacity)
-        d.resort_every = int(resort_every)
-        d.level_ratio = float(level_ratio)
-        d.lanes = int(lanes)
+        keep = []
+        d, n, geoms = _make_desc(x, r, keep, **kw)
+        self.geoms = geoms
+        self.n = n
+        self.dt = kw.get("dt", 1e-5)
+        self._create([d], keep, stream, use_torch)
+
+    def _create(self, descs, keep, stream, use_torch):
         self._alloc = None
         stream_ptr = None
         if use_torch:
             import torch
-            dev = torch.cuda.current_device()
-            self._alloc = _TorchAllocator(dev)
-            d.alloc, d.free_fn = self._alloc.alloc, self._alloc.free
+            self._alloc = _TorchAllocator(torch.cuda.current_device())
             if stream is None:
                 stream = torch.cuda.current_stream()
         if stream is not None:
             stream_ptr = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        arr = (dem_bed_desc * len(descs))(*descs)
+        for d in arr:
+            if self._alloc is not None:
+                d.alloc, d.free_fn = self._alloc.alloc, self._alloc.free
         self.stream = stream
-        self.n = n
-        self.dt = dt
-        _check(self.lib.dem_create_bed(C.byref(d), stream_ptr, C.byref(self._handle)))
+        if len(descs) == 1:
+            _check(self.lib.dem_create_bed(C.cast(arr, C.POINTER(dem_bed_desc)), stream_ptr, C.byref(self._handle)))
+        else:
+            _check(self.lib.dem_create_batch(C.cast(arr, C.POINTER(dem_bed_desc)), len(descs), stream_ptr,
+                                             C.byref(self._handle)))
         _live.add(self)
 
     # -- the C entry points -------------------------------------------------
     def step(self, nsteps=1):
         _check(self.lib.dem_step(self._handle, int(nsteps)))
+
+    def autotune(self, trial_steps=5):
+        """Pick the sweep layout and re-sort period by timing (dem_autotune)."""
+        a, b = C.c_int32(), C.c_int32()
+        _check(self.lib.dem_autotune(self._handle, int(trial_steps), C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def apply_plate_velocity(self, g, v, w=(0.0, 0.0, 0.0)):
         vv = (C.c_double * 3)(*map(float, v))
@@ -311,6 +337,35 @@ class Bed:
             self.close()
         except Exception:
             pass
+
+
+class Batch(Bed):
+    """Several independent beds advanced together (dem_create_batch).
+
+    beds: list of dicts with the keyword arguments of Bed (x, r, geoms, n_it,
+    ...); shared settings must agree.  Particle and primitive numbers are
+    global: bed k's come after those of beds 0..k-1 (see offsets)."""
+
+    def __init__(self, beds, *, stream=None, use_torch=True, **shared):
+        self.lib = load()
+        self._handle = C.c_void_p()
+        keep, descs = [], []
+        self.offsets, self.geom_offsets = [], []
+        n = ng = 0
+        self.geoms = []
+        for spec in beds:
+            kw = dict(shared)
+            kw.update({k: v for k, v in spec.items() if k not in ("x", "r")})
+            d, m, geoms = _make_desc(spec["x"], spec["r"], keep, **kw)
+            descs.append(d)
+            self.offsets.append(n)
+            self.geom_offsets.append(ng)
+            self.geoms += geoms
+            n += m
+            ng += len(geoms)
+        self.n = n
+        self.dt = shared.get("dt", 1e-5)
+        self._create(descs, keep, stream, use_torch)
 
 
 def detect_contacts_noalloc(pos, radius, key_a, key_b, delta, count, stream=None):

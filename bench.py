@@ -153,6 +153,8 @@ def run_gpu(args, rank, world):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     dev = torch.cuda.current_device()
+    # one dedicated stream for the bed, the L2 flush and the timing events
+    torch.cuda.set_stream(torch.cuda.Stream())
     spec = beds.refined_sinkage_bed()
     bed, top = settle_and_place(dem, spec, args.settle, args.lanes)
     pl = spec.plate
@@ -260,6 +262,7 @@ def run_batch(args):
     import torch
     from paper_2501_05300_gb300 import dem
     torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())   # every bed and event on one stream
     specs = beds.batch_specs()
     kws = []
     for k, s in enumerate(specs):

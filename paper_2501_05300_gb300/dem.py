@@ -243,6 +243,7 @@ class Bed:
             if stream is None:
                 stream = torch.cuda.current_stream()
         if stream is not None:
+            # a handle of 0 (the legacy default stream) makes the library use a stream of its own
             stream_ptr = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         arr = (dem_bed_desc * len(descs))(*descs)
         for d in arr:

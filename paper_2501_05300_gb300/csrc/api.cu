@@ -54,6 +54,7 @@ struct dem_bed {
     int n_geom = 0;
     int nbeds = 1;
     std::vector<LevelGrid> levels;   // host copy of the level table
+    std::vector<int> n_active;       // particles of beds still sweeping, per sweep
     std::vector<double> z_ref;  // particle surface under each primitive at creation
     // graphs: [parity][pre, jac, post]
     cudaGraphExec_t g[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -289,10 +290,25 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     std::vector<LevelGrid> levels;
     int max_nit = 0;
     int64_t total_cells = 0;
+    // Levels are laid out bed by bed in decreasing n_it, and the Morton re-sort
+    // orders particles by level: the particles still sweeping at sweep `it`
+    // then form a prefix of the slots, and each sweep launches over that prefix.
+    std::vector<int> border(nbeds);
+    std::vector<size_t> poff(nbeds);
+    std::vector<int> goff(nbeds);
+    for (int k = 0, o = 0, g = 0; k < nbeds; ++k) {
+        border[k] = k;
+        poff[k] = o;
+        goff[k] = g;
+        o += descs[k].n;
+        g += descs[k].n_geom;
+    }
+    std::stable_sort(border.begin(), border.end(), [&](int x, int y) { return descs[x].n_it > descs[y].n_it; });
     {
-        size_t o = 0;
-        int g0 = 0;
-        for (int k = 0; k < nbeds; ++k) {
+        for (int kk = 0; kk < nbeds; ++kk) {
+            const int k = border[kk];
+            const size_t o = poff[k];
+            const int g0 = goff[k];
             const dem_bed_desc& dk = descs[k];
             const int m = dk.n;
             max_nit = std::max(max_nit, dk.n_it);
@@ -375,10 +391,12 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
                 g.g1 = g0 + dk.n_geom;
                 total_cells += (int64_t)dims[0] * dims[1] * dims[2];
             }
-            g0 += dk.n_geom;
-            o += m;
         }
     }
+    // particles still sweeping at each sweep (a prefix after the first re-sort)
+    b->n_active.assign(std::max(max_nit, 1), 0);
+    for (int k = 0; k < nbeds; ++k)
+        for (int it = 0; it < descs[k].n_it; ++it) b->n_active[it] += descs[k].n;
     if (total_cells > (int64_t)(256 << 20)) {
         release(b);
         return fail(DEM_ERR_ARG, "broad-phase grids need %lld cells", (long long)total_cells);
@@ -595,7 +613,7 @@ static int body_pre(dem_bed* b, int p) {
 static int body_jac(dem_bed* b, int p) {
     int k = 0;
     if (b->P.n == 0) return 0;
-    for (int it = 0; it < b->P.n_it; ++it) k += launch_jacobi(b->P, b->B, p, it, b->stream);
+    for (int it = 0; it < b->P.n_it; ++it) k += launch_jacobi(b->P, b->B, p, it, b->n_active[it], b->stream);
     return k;
 }
 
@@ -952,6 +970,7 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
     P.n_it = d->n_it;   // every bed now takes n_it sweeps
     P.nit_uniform = 1;
     for (LevelGrid& g : b->levels) g.nit = d->n_it;
+    b->n_active.assign(std::max(d->n_it, 1), P.n);
     P.dt = d->dt;
     P.inv_dt = 1.0f / d->dt;
     P.e_H = d->e_H;

@@ -161,7 +161,8 @@ int launch_contacts_build(const SimParams& P, const DevBuf& B, int parity, cudaS
 int launch_inc_sort(const SimParams& P, const DevBuf& B, cudaStream_t s);
 int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
 int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
-int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s);
+// nact: particles of the beds still sweeping at sweep `it` (a prefix of the slots)
+int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int nact, cudaStream_t s);
 int launch_integrate(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
 int launch_resort(const SimParams& P, const DevBuf& B, cudaStream_t s);
 int launch_radix_sort(unsigned* key_a, int* val_a, unsigned* key_b, int* val_b, int n, int* hist,

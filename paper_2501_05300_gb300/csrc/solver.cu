@@ -417,12 +417,13 @@ int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s
 static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 static __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
-__global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, int p, int it) {
+__global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, int p, int it, int nact) {
     pdl_wait();
     pdl_trigger();
     if (*B.err) return;
     const int src = it & 1, dst = src ^ 1;
-    const int nc = min(B.own_start[p][P.n], P.max_contacts);
+    // contacts are stored in owner order: those of the active prefix come first
+    const int nc = min(B.own_start[p][nact], P.max_contacts);
     const VW* __restrict__ vin = B.vw[src];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         const int a = B.c_self[c], b = B.c_other[c];
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
 // BT lanes per body: lane l adds the body's shares l, l+BT, ...; the lane sums
 // are combined by a fixed butterfly, so the result does not depend on timing.
 #define BT 1
-__global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p, int it) {
+__global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p, int it, int nact) {
     pdl_wait();
     pdl_trigger();
     if (*B.err) return;
@@ -516,7 +517,8 @@ __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p
 }
 
 template <typename K>
-static void launch_pdl(K kernel, int blocks, cudaStream_t s, const SimParams& P, const DevBuf& B, int p, int it) {
+static void launch_pdl(K kernel, int blocks, cudaStream_t s, const SimParams& P, const DevBuf& B, int p, int it,
+                       int nact) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(SV_T);
@@ -526,7 +528,7 @@ static void launch_pdl(K kernel, int blocks, cudaStream_t s, const SimParams& P,
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, P, B, p, it);
+    cudaLaunchKernelEx(&cfg, kernel, P, B, p, it, nact);
 }
 
 static int sm_count() {
@@ -541,38 +543,40 @@ static int sm_count() {
 }
 
 template <int T>
-static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int it, bool update, cudaStream_t s) {
-    const int blocks = nblk(P.n * T, SV_T);
+static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int it, int nact, bool update,
+                         cudaStream_t s) {
+    const int blocks = nblk(nact * T, SV_T);
     if (update) k_sweep<T, true><<<blocks, SV_T, 0, s>>>(P, B, parity, it);
     else k_sweep<T, false><<<blocks, SV_T, 0, s>>>(P, B, parity, -1);
 }
 
-static void sweep_dispatch(const SimParams& P, const DevBuf& B, int parity, int it, bool update, cudaStream_t s) {
+static void sweep_dispatch(const SimParams& P, const DevBuf& B, int parity, int it, int nact, bool update,
+                           cudaStream_t s) {
     switch (P.lanes > 0 ? P.lanes : 2) {
-        case 1: sweep_launch<1>(P, B, parity, it, update, s); break;
-        case 2: sweep_launch<2>(P, B, parity, it, update, s); break;
-        case 8: sweep_launch<8>(P, B, parity, it, update, s); break;
-        default: sweep_launch<4>(P, B, parity, it, update, s); break;
+        case 1: sweep_launch<1>(P, B, parity, it, nact, update, s); break;
+        case 2: sweep_launch<2>(P, B, parity, it, nact, update, s); break;
+        case 8: sweep_launch<8>(P, B, parity, it, nact, update, s); break;
+        default: sweep_launch<4>(P, B, parity, it, nact, update, s); break;
     }
 }
 
 int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
     // v^0 from the warm-start impulses into velocities 0; a bed with no sweeps
     // keeps its warm start as the final impulse
-    sweep_dispatch(P, B, parity, -1, false, s);
+    sweep_dispatch(P, B, parity, -1, P.n, false, s);
     return 1;
 }
 
-int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s) {
+int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int nact, cudaStream_t s) {
     if (P.lanes > 0) {   // single-kernel sweep, T threads per body
-        sweep_dispatch(P, B, parity, it, true, s);
+        sweep_dispatch(P, B, parity, it, nact, true, s);
         return 1;
     }
     // two-pass sweep: contacts (grid-stride) then bodies
-    const int cblocks = std::min(nblk(P.max_contacts, SV_T), 16 * sm_count());
-    const int bblocks = nblk(P.n * BT, SV_T);
-    launch_pdl(k_contact_pass, cblocks, s, P, B, parity, it);
-    launch_pdl(k_body_pass, bblocks, s, P, B, parity, it);
+    const int cblocks = std::max(1, std::min(nblk(nact * 8, SV_T), 16 * sm_count()));
+    const int bblocks = nblk(nact * BT, SV_T);
+    launch_pdl(k_contact_pass, cblocks, s, P, B, parity, it, nact);
+    launch_pdl(k_body_pass, bblocks, s, P, B, parity, it, nact);
     return 2;
 }
 

@@ -128,6 +128,7 @@ def settle_and_place(dem, spec, settle_steps, lanes):
     hold.c = (pc.c[0], pc.c[1], pc.c[2] + 1.0)
     geoms[pl] = hold
     m = spec.material
+    lanes = max(lanes, 0)
     b = dem.Bed(spec.x, spec.r, geoms=geoms, rho=m.rho, mu_t=0.1, mu_r=0.01, n_it=N_IT, dt=2e-4,
                 lanes=lanes)
     b.step(settle_steps)
@@ -147,12 +148,12 @@ def settle_and_place(dem, spec, settle_steps, lanes):
     return b, top
 
 
-def fine_bed_squeezed():
+def fine_bed_squeezed(lx=1.82, ly=0.91):
     """The homogeneous fine bed (r = 2.5 mm, 10% spread) on a 1.82 x 0.91 m
     footprint (~4.0 M spheres; the 1.0 x 0.5 m bed holds ~1.2 M), its lattice
     squeezed to contact, and the 0.3 x 0.3 m plate with three grousers resting
     on the surface."""
-    spec = beds.fine_shear_bed(1.82, 0.91)
+    spec = beds.fine_shear_bed(lx, ly)
     c = spec.x.mean(0)
     x = c + (spec.x - c) * 0.84
     top = float((x[:, 2] + spec.r).max())
@@ -175,13 +176,15 @@ def run_fine(args):
     from paper_2501_05300_gb300 import dem
     torch.cuda.set_device(0)
     torch.cuda.set_stream(torch.cuda.Stream())
-    spec, x, geoms = fine_bed_squeezed()
+    spec, x, geoms = fine_bed_squeezed(*((0.91, 0.455) if args.fine_small else (1.82, 0.91)))
     nit = rules.n_iterations(rules.network_length_uniform(0.25, 5e-3), 0.02)
     m = spec.material
     bed = dem.Bed(x, spec.r, geoms=geoms, rho=m.rho, mu_t=m.mu_t, mu_r=m.mu_r, n_it=nit, dt=DT,
-                  lanes=args.lanes)
+                  lanes=max(args.lanes, 0))
     for gi in spec.plate_parts:
         bed.apply_plate_velocity(gi, (0.05, 0.0, 0.0))      # shear pull, 0.05 m/s
+    if args.lanes < 0:
+        bed.autotune(2)
     bed.step(args.warmup)
     bed.sync()
     bed.set_timing(True)
@@ -216,12 +219,17 @@ def run_gpu(args, rank, world):
     spec = beds.refined_sinkage_bed()
     bed, top = settle_and_place(dem, spec, args.settle, args.lanes)
     pl = spec.plate
+    if args.lanes < 0:                      # default: the autotuner picks the sweep layout
+        tuned = bed.autotune(3)
+    else:
+        tuned = (args.lanes, 20)
     bed.apply_plate_velocity(pl, (0.0, 0.0, -PLATE_V))
     bed.step(args.warmup)
     bed.sync()
     info = bed.info()
     n = info.n
     settled = (info.contacts + info.geom_contacts) / max(n, 1)
+    tuned = (info.lanes, info.resort_every)
     # L2 flush buffer (larger than the 129 MB L2), written between timed steps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -274,7 +282,7 @@ def run_gpu(args, rank, world):
     return dict(value=value, ms_per_step=ms_per_step, n=n, contacts=contacts, sweep_ms=sweep_ms,
                 alg_bytes=alg_bytes, achieved=achieved, peak=peak, launches=launches,
                 clocks=clk.summary(), e2e=e2e_value, force=f.tolist(), sinkage=sink, wall=wall,
-                settled=settled)
+                settled=settled, tuned=tuned)
 
 
 def squeezed_bed(lx, ly, squeeze=0.84):
@@ -379,8 +387,10 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--batch", action="store_true", help="the 36-bed batched-vs-sequential comparison")
     ap.add_argument("--fine", action="store_true", help="the ~4 M-sphere homogeneous fine bed")
+    ap.add_argument("--fine-small", action="store_true", help="with --fine: a quarter of the footprint (~1 M)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--lanes", type=int, default=0, help="threads per particle in the sweep (0: library default)")
+    ap.add_argument("--lanes", type=int, default=-1,
+                    help="sweep layout: -1 autotune (default), 0 two-pass, 1/2/4/8 threads per particle")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -439,7 +449,9 @@ def main():
         "config": {"workload": WORKLOAD, "particles": r["n"], "contacts": r["contacts"],
                    "n_it": N_IT, "dt": DT, "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MB write)",
-                   "contacts_per_particle_at_start": r["settled"]},
+                   "contacts_per_particle_at_start": r["settled"],
+                   "sweep_layout": "two-pass" if r["tuned"][0] == 0 else f"one kernel, {r['tuned'][0]} threads/particle",
+                   "resort_every": r["tuned"][1], "launch_params": "autotuner"},
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
                      "frac": r["achieved"] / r["peak"], "traffic": None,
                      "kernel": "k_jacobi (one projected Jacobi sweep)",

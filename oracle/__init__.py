@@ -14,5 +14,9 @@ Parity status per function (what pins it is in tests/test_oracle_*.py):
   Jacobi sweep                pinned: converges to the MCP solution found by an
                               independent projected Gauss-Seidel on tiny cases
   step-size / iteration rules pinned: Table 3 of the paper
+  gradient (torch_step.py)    pinned: its FP64 forward equals oracle.c step by
+                              step; its autograd gradient with respect to
+                              (k_n scale, mu_t, mu_r) equals central finite
+                              differences of oracle.c
 """
 from .binding import Oracle, OracleParams, Geom, detect, load, lib_path, build  # noqa: F401

@@ -321,3 +321,49 @@ def column(n, r=5e-3):
     """n equal spheres stacked on the floor plane, just touching."""
     x = np.array([[0.0, 0.0, r + 2 * r * k] for k in range(n)])
     return x, np.full(n, r, np.float32)
+
+
+# triaxial cell: wall indices of cell_walls()
+FLOOR, PLATEN, WALL_XLO, WALL_XHI, WALL_YLO, WALL_YHI = range(6)
+
+
+def cell_walls(lo, hi, v_top=0.0, mu_wall=0.0):
+    """The six walls of a box-shaped triaxial cell around [lo, hi]: floor, top
+    platen moving with velocity (0, 0, v_top), and four side walls.  Wall
+    friction and rolling resistance are zero in the paper's triaxial tests
+    (Sec. 3.2)."""
+    walls = [plane((0, 0, lo[2]), (0, 0, 1), mu_wall, mu_wall),
+             plane((0, 0, hi[2]), (0, 0, -1), mu_wall, mu_wall),
+             plane((lo[0], 0, 0), (1, 0, 0), mu_wall, mu_wall),
+             plane((hi[0], 0, 0), (-1, 0, 0), mu_wall, mu_wall),
+             plane((0, lo[1], 0), (0, 1, 0), mu_wall, mu_wall),
+             plane((0, hi[1], 0), (0, -1, 0), mu_wall, mu_wall)]
+    walls[PLATEN] = replace(walls[PLATEN], v=(0.0, 0.0, float(v_top)))
+    return walls
+
+
+def triaxial_cell(n=50_000, rmin=2.5e-3, rmax=3.0e-3, seed=2505, gap=0.01, squeeze=0.0, v_top=0.0):
+    """n spheres, r ~ U[rmin, rmax], on a jittered FCC lattice filling a cube,
+    inside the six walls of a box triaxial cell (Sec. 3.2).  `squeeze` > 0
+    scales the lattice about its centre by (1 - squeeze) so that neighbours
+    overlap, and moves every wall into the outermost spheres by squeeze * rmin:
+    a pre-stressed sample without a consolidation run."""
+    rng = np.random.default_rng(seed)
+    r_nom, spread = 0.5 * (rmin + rmax), (rmax - rmin) / (rmin + rmax)
+    a = 2 * rmax * (1 + gap)
+    side = a * (n / math.sqrt(2.0)) ** (1.0 / 3.0) + 2.0 * rmax
+    for _ in range(6):   # footprint whose stack height matches it
+        x, r, ztop = lattice_layer(np.random.default_rng(seed), side, side, 0.0, n, r_nom, spread, gap)
+        side *= (ztop / side) ** (1.0 / 3.0)
+    x, r, ztop = lattice_layer(rng, side, side, 0.0, n, r_nom, spread, gap)
+    if squeeze > 0:
+        c = 0.5 * (x.min(0) + x.max(0))
+        x = c + (x - c) * (1.0 - squeeze)
+    rr = r.astype(np.float64)[:, None]
+    inset = squeeze * rmin
+    lo = (x - rr).min(0) + inset
+    hi = (x + rr).max(0) - inset
+    mat = Material(rho=2600.0, mu_t=0.5, mu_r=0.02)
+    return Bed(x, r, cell_walls(lo, hi, v_top), mat, plate=PLATEN,
+               name=f"triaxial cell, {n} spheres r~U[{rmin * 1e3:g},{rmax * 1e3:g}] mm",
+               box=tuple(map(float, hi - lo)))

@@ -1,0 +1,88 @@
+"""Pins of the FP64 gradient oracle (oracle/torch_step.py).
+
+The autograd gradient is only as good as the forward it differentiates, so the
+forward is pinned to the C oracle (an independent implementation of the same
+step), and the gradient to central finite differences of the C oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import OracleParams
+from oracle import torch_step as ts
+from paper_2501_05300_gb300 import beds
+
+from dem_cases import oracle_geoms
+
+
+def cell(n=64, squeeze=0.015, v_top=-0.05, mu_wall=0.0, seed=2505):
+    b = beds.triaxial_cell(n, seed=seed, squeeze=squeeze, v_top=v_top)
+    geoms = beds.cell_walls(*_bounds(b), v_top=v_top, mu_wall=mu_wall) if mu_wall else b.geoms
+    return b.x, b.r.astype(np.float64), oracle_geoms(geoms)
+
+
+def _bounds(b):
+    lo = np.array([b.geoms[beds.WALL_XLO].c[0], b.geoms[beds.WALL_YLO].c[1], b.geoms[beds.FLOOR].c[2]])
+    hi = np.array([b.geoms[beds.WALL_XHI].c[0], b.geoms[beds.WALL_YHI].c[1], b.geoms[beds.PLATEN].c[2]])
+    return lo, hi
+
+
+def weights(ng=6, seed=1):
+    return np.random.default_rng(seed).normal(size=(ng, 3))
+
+
+def oracle_objective(p, x, r, geoms, steps, W):
+    o = oracle.Oracle(p, x, r, geoms=geoms)
+    J = 0.0
+    for _ in range(steps):
+        o.step(1)
+        J += sum(float(W[g] @ o.geom_force(g)[0]) for g in range(len(geoms)))
+    return J, o
+
+
+@pytest.mark.parametrize("mu_wall", [0.0, 0.3])
+def test_torch_forward_matches_c_oracle(mu_wall):
+    x, r, geoms = cell(mu_wall=mu_wall)
+    p = OracleParams(n_it=30)
+    steps = 6
+    W = weights()
+    J, o = oracle_objective(p, x, r, geoms, steps, W)
+    xo, vo, wo = o.state()
+    st = ts.TorchStepper(p, r, np.arange(len(r), dtype=np.int32), geoms)
+    th = [torch.tensor(v, dtype=torch.float64) for v in (p.kn_scale, p.mu_t, p.mu_r)]
+    Jt, xt, vt, wt = st.run(x, np.zeros_like(x), np.zeros_like(x), th, steps, W)
+    assert np.abs(xt.numpy() - xo).max() <= 1e-14
+    assert np.abs(vt.numpy() - vo).max() <= 1e-10 * max(1.0, np.abs(vo).max())
+    assert np.abs(wt.numpy() - wo).max() <= 1e-10 * max(1.0, np.abs(wo).max())
+    assert abs(float(Jt) - J) <= 1e-10 * abs(J)
+    assert abs(J) > 1.0   # the walls carry load
+
+
+@pytest.mark.parametrize("mu_wall,steps", [(0.0, 5), (0.3, 8)])
+def test_autograd_gradient_matches_c_oracle_fd(mu_wall, steps):
+    x, r, geoms = cell(mu_wall=mu_wall)
+    p = OracleParams(n_it=30)
+    W = weights()
+    th0 = np.array([p.kn_scale, p.mu_t, p.mu_r])
+    J, g = ts.gradient(p, x, r, np.zeros_like(x), np.zeros_like(x), geoms, th0, steps, W)
+    for k, name in enumerate(("kn_scale", "mu_t", "mu_r")):
+        h = 1e-5 * th0[k]
+        vals = []
+        for sgn in (1, -1):
+            th = th0.copy()
+            th[k] += sgn * h
+            q = OracleParams(n_it=30, kn_scale=th[0], mu_t=th[1], mu_r=th[2])
+            vals.append(oracle_objective(q, x, r, geoms, steps, W)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-5 * max(abs(fd), 1e-3 * abs(J)), (name, g[k], fd)
+
+
+def test_gradient_zero_without_contacts():
+    # spheres far from each other and from every wall: no force depends on theta
+    x, r, _ = cell()
+    x = x * 3.0
+    geoms = oracle_geoms(beds.cell_walls(x.min(0) - 0.1, x.max(0) + 0.1, v_top=-0.05))
+    p = OracleParams(n_it=10)
+    J, g = ts.gradient(p, x, r, np.zeros_like(x), np.zeros_like(x), geoms, (1.0, 0.5, 0.02), 3, weights())
+    assert J == 0.0 and np.all(g == 0.0)

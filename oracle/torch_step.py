@@ -51,9 +51,11 @@ class TorchStepper:
         self.inv_m = torch.as_tensor(inv_m, dtype=torch.float64) if inv_m is not None else 1.0 / m
         self.inv_I = torch.as_tensor(inv_I, dtype=torch.float64) if inv_I is not None else 1.0 / (0.4 * m * self.r ** 2)
 
-    def _contacts(self, x):
-        """Contact keys of the oracle's detection at positions x (no gradient)."""
-        geoms = [_b.Geom(g.type, g.c, g.R, g.he, g.v, g.w, g.E, g.nu, g.mu_t, g.mu_r) for g in self.planes]
+    def _contacts(self, x, plane_pos):
+        """Contact keys of the oracle's detection at positions x, with every
+        plane where it stands at the start of the step (no gradient)."""
+        geoms = [_b.Geom(g.type, tuple(float(q) for q in pp), g.R, g.he, g.v, g.w, g.E, g.nu, g.mu_t, g.mu_r)
+                 for g, pp in zip(self.planes, plane_pos)]
         ka, kb, _ = _b.detect(x.detach().numpy(), self.r.numpy(), self.ids, geoms)
         inv = np.empty(self.ids.max() + 1 if len(self.ids) else 1, np.int64)
         inv[self.ids] = np.arange(len(self.ids))
@@ -71,7 +73,7 @@ class TorchStepper:
         P = self.p
         h, ups = P.dt, 1.0 / (1.0 + 4.0 * P.damp_steps)
         kns, mu_t, mu_r = theta
-        keys, a, b, ga, gg = self._contacts(x)
+        keys, a, b, ga, gg = self._contacts(x, plane_pos)
         nb = len(a)
         ng_c = len(ga)
         N = x.shape[0]

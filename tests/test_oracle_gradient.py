@@ -32,8 +32,8 @@ def weights(ng=6, seed=1):
     return np.random.default_rng(seed).normal(size=(ng, 3))
 
 
-def oracle_objective(p, x, r, geoms, steps, W):
-    o = oracle.Oracle(p, x, r, geoms=geoms)
+def oracle_objective(p, x, r, geoms, steps, W, v0=None):
+    o = oracle.Oracle(p, x, r, v0, geoms=geoms)
     J = 0.0
     for _ in range(steps):
         o.step(1)
@@ -41,17 +41,23 @@ def oracle_objective(p, x, r, geoms, steps, W):
     return J, o
 
 
-@pytest.mark.parametrize("mu_wall", [0.0, 0.3])
-def test_torch_forward_matches_c_oracle(mu_wall):
-    x, r, geoms = cell(mu_wall=mu_wall)
+def moving(x, vmax=0.05, seed=5):
+    return np.random.default_rng(seed).uniform(-vmax, vmax, x.shape)
+
+
+@pytest.mark.parametrize("mu_wall,v_top,vmax,steps", [(0.0, -0.05, 0.0, 6), (0.3, -0.05, 0.0, 6),
+                                                      (0.3, -1.0, 0.05, 12)])
+def test_torch_forward_matches_c_oracle(mu_wall, v_top, vmax, steps):
+    # the fast platen (10 um per step) moves contacts with it; the particles start moving
+    x, r, geoms = cell(mu_wall=mu_wall, v_top=v_top)
+    v0 = moving(x, vmax)
     p = OracleParams(n_it=30)
-    steps = 6
     W = weights()
-    J, o = oracle_objective(p, x, r, geoms, steps, W)
+    J, o = oracle_objective(p, x, r, geoms, steps, W, v0)
     xo, vo, wo = o.state()
     st = ts.TorchStepper(p, r, np.arange(len(r), dtype=np.int32), geoms)
     th = [torch.tensor(v, dtype=torch.float64) for v in (p.kn_scale, p.mu_t, p.mu_r)]
-    Jt, xt, vt, wt = st.run(x, np.zeros_like(x), np.zeros_like(x), th, steps, W)
+    Jt, xt, vt, wt = st.run(x, v0, np.zeros_like(x), th, steps, W)
     assert np.abs(xt.numpy() - xo).max() <= 1e-14
     assert np.abs(vt.numpy() - vo).max() <= 1e-10 * max(1.0, np.abs(vo).max())
     assert np.abs(wt.numpy() - wo).max() <= 1e-10 * max(1.0, np.abs(wo).max())
@@ -59,13 +65,16 @@ def test_torch_forward_matches_c_oracle(mu_wall):
     assert abs(J) > 1.0   # the walls carry load
 
 
-@pytest.mark.parametrize("mu_wall,steps", [(0.0, 5), (0.3, 8)])
-def test_autograd_gradient_matches_c_oracle_fd(mu_wall, steps):
-    x, r, geoms = cell(mu_wall=mu_wall)
+@pytest.mark.parametrize("mu_wall,v_top,vmax,steps", [(0.0, -0.05, 0.0, 5), (0.3, -0.05, 0.0, 8),
+                                                      (0.3, -1.0, 0.05, 10)])
+def test_autograd_gradient_matches_c_oracle_fd(mu_wall, v_top, vmax, steps):
+    x, r, geoms = cell(n=200 if vmax else 64, mu_wall=mu_wall, v_top=v_top)
+    v0 = moving(x, vmax)
     p = OracleParams(n_it=30)
     W = weights()
     th0 = np.array([p.kn_scale, p.mu_t, p.mu_r])
-    J, g = ts.gradient(p, x, r, np.zeros_like(x), np.zeros_like(x), geoms, th0, steps, W)
+    J, g = ts.gradient(p, x, r, v0, np.zeros_like(x), geoms, th0, steps, W)
+    fds = []
     for k, name in enumerate(("kn_scale", "mu_t", "mu_r")):
         h = 1e-5 * th0[k]
         vals = []
@@ -73,9 +82,14 @@ def test_autograd_gradient_matches_c_oracle_fd(mu_wall, steps):
             th = th0.copy()
             th[k] += sgn * h
             q = OracleParams(n_it=30, kn_scale=th[0], mu_t=th[1], mu_r=th[2])
-            vals.append(oracle_objective(q, x, r, geoms, steps, W)[0])
-        fd = (vals[0] - vals[1]) / (2 * h)
-        assert abs(g[k] - fd) <= 1e-5 * max(abs(fd), 1e-3 * abs(J)), (name, g[k], fd)
+            vals.append(oracle_objective(q, x, r, geoms, steps, W, v0)[0])
+        fds.append((vals[0] - vals[1]) / (2 * h))
+    # a stencil of +-1e-5 may still straddle a stick/slip switch of one contact:
+    # 1e-4 of the component plus 1e-6 of the largest one
+    fds = np.array(fds)
+    assert np.all(np.abs(g - fds) <= 1e-4 * np.abs(fds) + 1e-6 * np.abs(fds).max()), (g, fds)
+    if vmax:   # sliding and rolling contacts: every parameter matters
+        assert np.all(np.abs(fds) > 1e-3 * np.abs(fds).max())
 
 
 def test_gradient_zero_without_contacts():

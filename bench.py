@@ -378,6 +378,146 @@ def run_batch(args):
                 identical_to_sequential=same)
 
 
+# differentiation workload: box triaxial cell (Sec. 3.2)
+TRIAX_N = 50_000
+TRIAX_SIGMA = 100e3      # confining pressure [Pa]
+TRIAX_RATE = 0.5         # axial strain rate [1/s]
+TRIAX_STEPS = 400
+TRIAX_CKPT = 20
+TRIAX_WORKLOAD = ("triaxial cell: 50k spheres r~U[2.5,3.0] mm, consolidated to 100 kPa, axial strain rate "
+                  "0.5/s, dt 1e-5 s; d(mean deviatoric stress over 400 steps)/d(k_n scale, mu_t, mu_r), "
+                  "checkpoints every 20 steps")
+
+
+def _wall_stress(bed, walls=range(6)):
+    """Normal stress on each wall of the cell [Pa] (compression positive)."""
+    c = [np.array(bed.read_geom(g).c[:]) for g in range(6)]
+    lo = np.array([c[beds.WALL_XLO][0], c[beds.WALL_YLO][1], c[beds.FLOOR][2]])
+    hi = np.array([c[beds.WALL_XHI][0], c[beds.WALL_YHI][1], c[beds.PLATEN][2]])
+    L = hi - lo
+    area = {beds.FLOOR: L[0] * L[1], beds.PLATEN: L[0] * L[1], beds.WALL_XLO: L[1] * L[2],
+            beds.WALL_XHI: L[1] * L[2], beds.WALL_YLO: L[0] * L[2], beds.WALL_YHI: L[0] * L[2]}
+    out = {}
+    for g in walls:
+        nrm = np.array(bed.geoms[g].R)[[2, 5, 8]]     # inward normal
+        f = bed.read_forces(g)[0]
+        out[g] = float(-(f @ nrm) / area[g])
+    return out, L
+
+
+def _servo(bed, walls, target, vmax):
+    """Move each wall along its inward normal at vmax (target - sigma)/target,
+    clipped to +-vmax."""
+    sig, L = _wall_stress(bed, walls)
+    for g in walls:
+        nrm = np.array(bed.geoms[g].R)[[2, 5, 8]]
+        u = vmax * float(np.clip((target - sig[g]) / target, -1.0, 1.0))
+        bed.apply_plate_velocity(g, tuple(u * nrm))
+    return sig, L
+
+
+def prepare_triaxial(dem, lanes=0, n=TRIAX_N, seed=2505, max_steps=8000):
+    """Isotropic consolidation, then the start of drained shearing.
+    Consolidation (Sec. 3.1 generation friction mu_t 0.1, mu_r 0.01, no
+    gravity, dt 5e-5 from Eq. 9 at 100 kPa, 60 sweeps): all six walls servo to
+    100 kPa.  Shearing (test friction, dt 1e-5, N_it from Eq. 8 with n_d =
+    h/d): the platen moves down at strain rate 0.5/s while the side walls keep
+    servoing to 100 kPa for 300 steps."""
+    spec = beds.triaxial_cell(n, seed=seed)
+    m = spec.material
+    bed = dem.Bed(spec.x, spec.r, geoms=spec.geoms, rho=m.rho, mu_t=0.1, mu_r=0.01, n_it=60, dt=5e-5,
+                  gravity=(0.0, 0.0, 0.0), lanes=lanes)
+    steps, ok = 0, 0
+    while steps < max_steps:
+        sig, L = _servo(bed, range(6), TRIAX_SIGMA, 0.05)
+        bed.step(10)
+        steps += 10
+        ok = ok + 1 if all(abs(v - TRIAX_SIGMA) < 0.03 * TRIAX_SIGMA for v in sig.values()) else 0
+        if ok >= 10:
+            break
+    for g in range(6):
+        bed.apply_plate_velocity(g, (0.0, 0.0, 0.0))
+    h = float(L[2])
+    nit = rules.n_iterations(rules.network_length_uniform(h, 2 * 2.75e-3), 0.02)
+    bed.set_params(dt=DT, n_it=nit, mu_t=m.mu_t, mu_r=m.mu_r, gravity=(0.0, 0.0, 0.0), lanes=lanes)
+    side = [beds.WALL_XLO, beds.WALL_XHI, beds.WALL_YLO, beds.WALL_YHI]
+    for _ in range(15):
+        sig, L = _servo(bed, side, TRIAX_SIGMA, 0.05)
+        bed.apply_plate_velocity(beds.PLATEN, (0.0, 0.0, -TRIAX_RATE * float(L[2])))
+        bed.step(20)
+    for g in side:                       # side walls held during the differentiated window
+        bed.apply_plate_velocity(g, (0.0, 0.0, 0.0))
+    sig, L = _wall_stress(bed)
+    return bed, dict(consolidation_steps=steps, n_it=nit, height=h, stress=sig)
+
+
+def run_triaxial(args):
+    """Cost of the gradient of the mean deviatoric stress over a 400-step
+    window against the plain forward of the same window, and the gradient's
+    check against central differences (h = 1e-3 relative) of the forward."""
+    import torch
+    from paper_2501_05300_gb300 import dem
+    from paper_2501_05300_gb300.adjoint import CellGeometry, deviatoric_stress, geom_forces
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    t_prep = time.perf_counter()
+    bed, prep = prepare_triaxial(dem, lanes=max(args.lanes, 0))
+    if args.lanes < 0:
+        bed.autotune(2)
+    t_prep = time.perf_counter() - t_prep
+    theta0 = (1.0, 0.5, 0.02)
+    bed.set_material(kn_scale=theta0[0], mu_t=theta0[1], mu_r=theta0[2])
+    bed.step(args.warmup)
+    start = bed.save_checkpoint()
+    cell = CellGeometry.from_bed(bed)
+    info = bed.info()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        t0 = time.perf_counter()
+        out = fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return out, max(ev[0].elapsed_time(ev[1]) * 1e-3, time.perf_counter() - t0)
+
+    with ClockSampler(0) as clk:
+        _, t_fwd = timed(lambda: bed.step(TRIAX_STEPS))
+        bed.restore_checkpoint(start)
+        theta = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+        F, t_rec = timed(lambda: geom_forces(bed, theta, TRIAX_STEPS, TRIAX_CKPT))
+        J = deviatoric_stress(F, cell).mean()
+        _, t_adj = timed(lambda: J.backward())
+    grad = theta.grad.numpy().copy()
+    mem = torch.cuda.max_memory_allocated() / 2 ** 30
+
+    def objective(th):
+        bed.restore_checkpoint(start)
+        bed.set_material(kn_scale=th[0], mu_t=th[1], mu_r=th[2])
+        Fk = bed.record(TRIAX_STEPS, TRIAX_STEPS)
+        return float(deviatoric_stress(torch.from_numpy(Fk), cell).mean())
+
+    fd = []
+    for k in range(3):
+        h = 1e-3 * theta0[k]
+        tp, tm = list(theta0), list(theta0)
+        tp[k] += h
+        tm[k] -= h
+        fd.append((objective(tp) - objective(tm)) / (2 * h))
+    fd = np.array(fd)
+    contacts = info.contacts + info.geom_contacts
+    bed.free_checkpoint(start)
+    bed.close()
+    return dict(adjoint_over_forward=t_adj / t_fwd, record_over_forward=t_rec / t_fwd,
+                gradient_over_forward=(t_rec + t_adj) / t_fwd, forward_s=t_fwd, record_s=t_rec,
+                adjoint_s=t_adj, J=float(J.detach()), grad=grad.tolist(), fd=fd.tolist(),
+                fd_rel_err=(np.abs(grad - fd) / np.abs(fd).max()).tolist(), particles=info.n,
+                contacts=contacts, peak_mem_gib=mem, prepare_s=t_prep, clocks=clk.summary(),
+                sweep_layout=info.lanes, **prep)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,6 +528,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="the 36-bed batched-vs-sequential comparison")
     ap.add_argument("--fine", action="store_true", help="the ~4 M-sphere homogeneous fine bed")
     ap.add_argument("--fine-small", action="store_true", help="with --fine: a quarter of the footprint (~1 M)")
+    ap.add_argument("--triaxial", action="store_true",
+                    help="adjoint cost and gradient check on the 50k triaxial cell")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=-1,
                     help="sweep layout: -1 autotune (default), 0 two-pass, 1/2/4/8 threads per particle")
@@ -421,6 +563,14 @@ def main():
                           "higher_is_better": True, "steps": args.steps, "data": "synthetic",
                           "config": {"workload": "36 refined beds (6x6 grid), one object vs one by one",
                                      **{k: v for k, v in r.items() if k != "speedup"}}}))
+        return
+    if args.triaxial:
+        r = run_triaxial(args)
+        print(json.dumps({"metric": "adjoint/fwd cost", "value": r["adjoint_over_forward"], "unit": "x",
+                          "higher_is_better": False, "n_gpus": 1, "steps": TRIAX_STEPS, "warmup": args.warmup,
+                          "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": TRIAX_WORKLOAD, "ckpt_every": TRIAX_CKPT,
+                                     **{k: v for k, v in r.items() if k != "adjoint_over_forward"}}}))
         return
     if args.fine:
         r = run_fine(args)

@@ -198,6 +198,53 @@ dem_status dem_read_timing(dem_bed* bed, double* step_ms, double* jacobi_ms, int
  * (the test phase starts here).  Synchronises; the per-step graphs are rebuilt. */
 dem_status dem_set_params(dem_bed* bed, const dem_bed_desc* desc);
 
+/* ---- differentiation (reverse mode) -------------------------------------
+ * Gradients of J = sum_t sum_g dJ_dF[t][g] . F_t,g, a linear functional of
+ * the force on every primitive in every step, with respect to the scale s_k of
+ * the normal stiffness k_n = s_k E* sqrt(d*) / 3 (Sec. 2.2, all contacts), the
+ * particle-particle friction coefficient mu_t (Eq. 6) and the particle-particle
+ * rolling-resistance coefficient mu_r (Eq. 7).  The derivative is taken along
+ * the contact set of every recorded step (fixed topology per step); contacts
+ * that open or close inside the window are not differentiated.
+ *
+ * dem_record: advance the bed nsteps steps (as dem_step) and keep a checkpoint
+ * of its state every ckpt_every steps.  forces (may be NULL): host or device
+ * buffer of nsteps * n_geom * 3 doubles, the force on each primitive in each
+ * step [N], the same numbers dem_read_forces returns after that step.
+ * Synchronises.  Requirements: every primitive is a plane that does not spin,
+ * every bed of the object takes the same n_it; else DEM_ERR_ARG.  Memory:
+ * one checkpoint (positions, velocities, warm start: about 100 B per particle
+ * and 40 B per contact) per ckpt_every steps.
+ *
+ * dem_step_adjoint: the gradient for the last recorded window.  dJ_dF: host or
+ * device buffer shaped like `forces`.  grad[3] (host) receives dJ/ds_k,
+ * dJ/dmu_t, dJ/dmu_r.  Each segment of ckpt_every steps is recomputed from its
+ * checkpoint with a tape of every Jacobi iterate (24 B per contact and 32 B
+ * per particle per sweep, for the ckpt_every steps of one segment), then
+ * reversed.  The bed is left in the state after the window, so stepping may
+ * continue, and the call may be repeated with other dJ_dF.  DEM_ERR_STATE if
+ * nothing was recorded, the bed was stepped since, or settings changed.
+ * Synchronises.  No counterpart in the paper, which does not differentiate its
+ * simulations; the step it reverses is the paper's. */
+dem_status dem_record(dem_bed* bed, int32_t nsteps, int32_t ckpt_every, double* forces);
+dem_status dem_step_adjoint(dem_bed* bed, const double* dJ_dF, double grad[3]);
+
+/* ---- whole-state checkpoints -----------------------------------------------
+ * dem_checkpoint_save: a device copy of everything the next step reads
+ * (positions, velocities, slot order, primitive poses and velocities, the last
+ * step's impulses that warm-start the next) plus the last step's geometry
+ * forces.  dem_checkpoint_restore puts the bed back into that state; stepping
+ * from it repeats the original steps bit for bit (under the same settings;
+ * settings changed with dem_set_params since the save stay in force).  A
+ * restore ends a window recorded with dem_record.  Checkpoints belong to their
+ * bed (DEM_ERR_ARG for another bed); free them with dem_checkpoint_free before
+ * dem_destroy_bed.  Memory: about 100 B per particle and 40 B per contact, from
+ * the bed's allocator.  Synchronise.  No counterpart in the paper. */
+typedef struct dem_checkpoint dem_checkpoint;
+dem_status dem_checkpoint_save(dem_bed* bed, dem_checkpoint** out);
+dem_status dem_checkpoint_restore(dem_bed* bed, const dem_checkpoint* ckpt);
+dem_status dem_checkpoint_free(dem_bed* bed, dem_checkpoint* ckpt);
+
 /* Release all device memory of the bed.  NULL is accepted. */
 dem_status dem_destroy_bed(dem_bed* bed);
 

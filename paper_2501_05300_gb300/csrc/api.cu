@@ -16,11 +16,21 @@
 #include <string>
 #include <vector>
 
-#include "dem_internal.cuh"
+#include "bed.cuh"
 
 static thread_local std::string g_err;
 
 static dem_status fail(dem_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+dem_status dem_fail(dem_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -38,35 +48,8 @@ static dem_status fail(dem_status st, const char* fmt, ...) {
                         __FILE__, __LINE__);                                             \
     } while (0)
 
-struct dem_bed {
-    int dev = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    SimParams P{};
-    DevBuf B{};
-    int resort_every = 20;
-    int64_t steps = 0;
-    bool faulted = false;
-    dem_alloc_fn alloc = nullptr;
-    dem_free_fn freef = nullptr;
-    void* actx = nullptr;
-    std::vector<void*> allocs;
-    int n_geom = 0;
-    int nbeds = 1;
-    std::vector<LevelGrid> levels;   // host copy of the level table
-    std::vector<int> n_active;       // particles of beds still sweeping, per sweep
-    std::vector<double> z_ref;  // particle surface under each primitive at creation
-    // graphs: [parity][pre, jac, post]
-    cudaGraphExec_t g[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-    cudaGraphExec_t g_resort = nullptr;
-    int k_step = 0, k_resort = 0;
-    // timing
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<cudaEvent_t> ev_used;   // 4 per timed step: start, Jacobi start, Jacobi end, end
-    double t_step_ms = 0, t_jac_ms = 0;
-    int64_t t_steps = 0;
-};
+
+
 
 // ---------------------------------------------------------------------------
 // memory
@@ -86,6 +69,20 @@ static dem_status dalloc(dem_bed* b, void** p, size_t bytes) {
     return DEM_OK;
 }
 
+dem_status dem_dalloc(dem_bed* b, void** p, size_t bytes) { return dalloc(b, p, bytes); }
+
+void dem_dfree(dem_bed* b, void* p) {
+    if (!p) return;
+    for (size_t k = 0; k < b->allocs.size(); ++k)
+        if (b->allocs[k] == p) {
+            b->allocs[k] = b->allocs.back();
+            b->allocs.pop_back();
+            break;
+        }
+    if (b->freef) b->freef(p, b->actx, (void*)b->stream);
+    else cudaFreeAsync(p, b->stream);
+}
+
 template <typename T>
 static dem_status dalloc_n(dem_bed* b, T** p, size_t count) {
     return dalloc(b, (void**)p, count * sizeof(T));
@@ -99,6 +96,7 @@ static void release(dem_bed* b) {
         for (int k = 0; k < 3; ++k)
             if (b->g[p][k]) cudaGraphExecDestroy(b->g[p][k]);
     if (b->g_resort) cudaGraphExecDestroy(b->g_resort);
+    dem_adjoint_release(b);
     for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : b->ev_used) cudaEventDestroy(e);
     for (void* p : b->allocs) {
@@ -689,6 +687,19 @@ static dem_status check_fault(dem_bed* b) {
     return DEM_OK;
 }
 
+dem_status dem_check_fault(dem_bed* b) { return check_fault(b); }
+
+dem_status dem_launch_step(dem_bed* b) {
+    const bool resort = b->g_resort && b->steps % b->resort_every == 0;
+    const int p = (int)(b->steps & 1);
+    if (resort) CK(cudaGraphLaunch(b->g_resort, b->stream));
+    CK(cudaGraphLaunch(b->g[p][0], b->stream));
+    if (b->g[p][1]) CK(cudaGraphLaunch(b->g[p][1], b->stream));
+    if (b->g[p][2]) CK(cudaGraphLaunch(b->g[p][2], b->stream));
+    b->steps++;
+    return DEM_OK;
+}
+
 extern "C" dem_status dem_step(dem_bed* b, int32_t nsteps) {
     g_err.clear();
     if (!b) return fail(DEM_ERR_ARG, "bed is NULL");
@@ -711,13 +722,11 @@ extern "C" dem_status dem_step(dem_bed* b, int32_t nsteps) {
             CK(cudaEventRecord(take_event(b), b->stream));
             if (b->g[p][2]) CK(cudaGraphLaunch(b->g[p][2], b->stream));
             CK(cudaEventRecord(take_event(b), b->stream));
+            b->steps++;
         } else {
-            if (resort) CK(cudaGraphLaunch(b->g_resort, b->stream));
-            CK(cudaGraphLaunch(b->g[p][0], b->stream));
-            if (b->g[p][1]) CK(cudaGraphLaunch(b->g[p][1], b->stream));
-            if (b->g[p][2]) CK(cudaGraphLaunch(b->g[p][2], b->stream));
+            dem_status st = dem_launch_step(b);
+            if (st != DEM_OK) return st;
         }
-        b->steps++;
     }
     return DEM_OK;
 }

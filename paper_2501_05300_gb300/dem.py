@@ -26,8 +26,9 @@ PLANE, BOX, CYLINDER = 0, 1, 2
 # every entry point declared in include/dem.h
 EXPORTS = ("dem_create_bed", "dem_create_batch", "dem_autotune", "dem_step", "dem_apply_plate_velocity", "dem_read_forces",
            "dem_read_state", "dem_read_contacts", "dem_read_geom", "dem_sync", "dem_get_info",
-           "dem_set_timing", "dem_read_timing", "dem_set_params", "dem_destroy_bed",
-           "dem_detect_contacts_noalloc", "dem_last_error")
+           "dem_set_timing", "dem_read_timing", "dem_set_params", "dem_record", "dem_step_adjoint",
+           "dem_checkpoint_save", "dem_checkpoint_restore", "dem_checkpoint_free",
+           "dem_destroy_bed", "dem_detect_contacts_noalloc", "dem_last_error")
 
 
 class DemError(RuntimeError):
@@ -110,6 +111,11 @@ def load(build: bool = True):
         "dem_set_timing": (i32, [vp, i32]),
         "dem_read_timing": (i32, [vp, dp, dp, C.POINTER(C.c_int64)]),
         "dem_set_params": (i32, [vp, C.POINTER(dem_bed_desc)]),
+        "dem_record": (i32, [vp, i32, i32, vp]),
+        "dem_step_adjoint": (i32, [vp, vp, dp]),
+        "dem_checkpoint_save": (i32, [vp, C.POINTER(vp)]),
+        "dem_checkpoint_restore": (i32, [vp, vp]),
+        "dem_checkpoint_free": (i32, [vp, vp]),
         "dem_destroy_bed": (i32, [vp]),
         "dem_detect_contacts_noalloc": (i32, [i32, vp, vp, i64, vp, vp, vp, vp, vp]),
         "dem_last_error": (C.c_char_p, []),
@@ -218,6 +224,14 @@ def _make_desc(x, r, keep, *, v=None, w=None, geoms=(), rho=2600.0, E=1e9, nu=0.
     return d, n, geoms
 
 
+_SOLVER_KEYS = dict(dt=1e-5, n_it=100, mu_t=0.5, mu_r=0.02, damp_steps=4.5, e_H=1.25,
+                    gravity=(0.0, 0.0, -9.81), kn_scale=1.0, eps_reg=1e-6)
+
+
+def _solver_params(kw):
+    return {k: kw.get(k, v) for k, v in _SOLVER_KEYS.items()}
+
+
 class Bed:
     """A bed of spheres advanced by the CUDA library.
 
@@ -232,10 +246,12 @@ class Bed:
         self.geoms = geoms
         self.n = n
         self.dt = kw.get("dt", 1e-5)
+        self.params = _solver_params(kw)
         self._create([d], keep, stream, use_torch)
 
     def _create(self, descs, keep, stream, use_torch):
         self._alloc = None
+        self._ckpts = []
         stream_ptr = None
         if use_torch:
             import torch
@@ -327,9 +343,55 @@ class Bed:
         d.kn_scale, d.eps_reg, d.lanes = kn_scale, eps_reg, int(lanes)
         _check(self.lib.dem_set_params(self._handle, C.byref(d)))
         self.dt = dt
+        self.params = dict(dt=dt, n_it=int(n_it), mu_t=mu_t, mu_r=mu_r, damp_steps=damp_steps, e_H=e_H,
+                           gravity=tuple(gravity), kn_scale=kn_scale, eps_reg=eps_reg)
+
+    def set_material(self, *, kn_scale=None, mu_t=None, mu_r=None):
+        """Change the stiffness scale and the friction coefficients only; the
+        sweep layout is kept."""
+        p = dict(self.params)
+        for k, v in (("kn_scale", kn_scale), ("mu_t", mu_t), ("mu_r", mu_r)):
+            if v is not None:
+                p[k] = float(v)
+        if all(p[k] == self.params[k] for k in ("kn_scale", "mu_t", "mu_r")):
+            return
+        self.set_params(**p, lanes=-1)
+
+    def record(self, nsteps, ckpt_every=20):
+        """Advance nsteps steps keeping checkpoints for the adjoint
+        (dem_record).  Returns the force on every primitive in every step,
+        shape (nsteps, n_geom, 3) [N]."""
+        f = np.zeros((int(nsteps), len(self.geoms), 3), np.float64)
+        _check(self.lib.dem_record(self._handle, int(nsteps), int(ckpt_every), _ptr(f)))
+        return f
+
+    def save_checkpoint(self):
+        """A device copy of the bed's state (dem_checkpoint_save)."""
+        h = C.c_void_p()
+        _check(self.lib.dem_checkpoint_save(self._handle, C.byref(h)))
+        self._ckpts.append(h)
+        return h
+
+    def restore_checkpoint(self, h):
+        _check(self.lib.dem_checkpoint_restore(self._handle, h))
+
+    def free_checkpoint(self, h):
+        _check(self.lib.dem_checkpoint_free(self._handle, h))
+        self._ckpts = [c for c in self._ckpts if c.value != h.value]
+
+    def adjoint(self, dJ_dF):
+        """dJ/d(kn_scale, mu_t, mu_r) of J = sum dJ_dF * F over the recorded
+        window (dem_step_adjoint)."""
+        w = _input(dJ_dF, np.float64, (-1, len(self.geoms), 3))
+        g = (C.c_double * 3)()
+        _check(self.lib.dem_step_adjoint(self._handle, _ptr(w), g))
+        return np.array(g[:])
 
     def close(self):
         if getattr(self, "_handle", None) and self._handle.value:
+            for h in getattr(self, "_ckpts", []):
+                self.lib.dem_checkpoint_free(self._handle, h)
+            self._ckpts = []
             self.lib.dem_destroy_bed(self._handle)
             self._handle = C.c_void_p()
 
@@ -366,6 +428,7 @@ class Batch(Bed):
             ng += len(geoms)
         self.n = n
         self.dt = shared.get("dt", 1e-5)
+        self.params = _solver_params(shared)
         self._create(descs, keep, stream, use_torch)
 
 

@@ -624,15 +624,25 @@ __global__ void __launch_bounds__(AD_T) k_adj_state(SimParams P, TapeStep T, Adj
     block_sum3(gk, 0.0, 0.0, Q.part + 3 * AD_RED_BLOCKS);
 }
 
-// grad += partial sums, in a fixed order
-__global__ void k_adj_reduce(const double* part, int nb1, int nb2, double* grad) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// grad += partial sums: thread t adds partials t, t + 256, ... in order, then a
+// fixed tree; the result does not depend on timing
+#define AD_RED_T 256
+__global__ void __launch_bounds__(AD_RED_T) k_adj_reduce(const double* part, int nb1, int nb2, double* grad) {
+    __shared__ double sm[3][AD_RED_T];
     double g[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < nb1; ++b)
-        for (int q = 0; q < 3; ++q) g[q] += part[3 * b + q];
-    for (int b = 0; b < nb2; ++b)
-        for (int q = 0; q < 3; ++q) g[q] += part[3 * AD_RED_BLOCKS + 3 * b + q];
-    for (int q = 0; q < 3; ++q) grad[q] += g[q];
+    for (int b = threadIdx.x; b < nb1 + nb2; b += AD_RED_T) {
+        const double* p = b < nb1 ? part + 3 * b : part + 3 * AD_RED_BLOCKS + 3 * (b - nb1);
+        for (int q = 0; q < 3; ++q) g[q] += p[q];
+    }
+    for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] = g[q];
+    __syncthreads();
+    for (int o = AD_RED_T / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) grad[q] += sm[q][0];
 }
 
 // ---------------------------------------------------------------------------
@@ -870,7 +880,7 @@ static dem_status reverse_step(dem_bed* b, const TapeStep& T, int cur, int widx)
     k_adj_rows<<<AD_RED_BLOCKS, AD_T, 0, s>>>(P, T, Q);
     const int sb = nblk(n, AD_T);
     k_adj_state<<<sb, AD_T, 0, s>>>(P, T, Q);
-    k_adj_reduce<<<1, 32, 0, s>>>(S->part, AD_RED_BLOCKS, sb, S->grad);
+    k_adj_reduce<<<1, AD_RED_T, 0, s>>>(S->part, AD_RED_BLOCKS, sb, S->grad);
     DEM_CK(cudaGetLastError());
     return DEM_OK;
 }

@@ -417,7 +417,9 @@ int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s
 static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 static __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
-__global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, int p, int it, int nact) {
+// 12 resident blocks per SM (42 registers): the pass is latency-bound, more
+// warps in flight beat the few spilled bytes
+__global__ void __launch_bounds__(SV_T, 12) k_contact_pass(SimParams P, DevBuf B, int p, int it, int nact) {
     pdl_wait();
     pdl_trigger();
     if (*B.err) return;
@@ -432,8 +434,9 @@ __global__ void __launch_bounds__(SV_T) k_contact_pass(SimParams P, DevBuf B, in
         const bool last = it == nit - 1;
         const int2 pos = B.c_pos[c];
         const float4 r0 = B.rec[3 * (size_t)c], r1 = B.rec[3 * (size_t)c + 1], r2 = B.rec[3 * (size_t)c + 2];
-        const float4 l0 = B.lamA[src][c];
-        const float2 l1 = B.lamB[src][c];
+        // the previous iterate is dead after this read: stream it (evict first)
+        const float4 l0 = __ldcs(&B.lamA[src][c]);
+        const float2 l1 = __ldcs(&B.lamB[src][c]);
         const VW A = vin[a], Bv = vin[b];
         const float3 va = f3(A.v), wa = f3(A.w), vb = f3(Bv.v), wb = f3(Bv.w);
         const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, va - vb, wa, wb, P.eps_reg);
@@ -474,9 +477,11 @@ __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p
     if (active) {
         const int e1 = B.inc_start[i + 1];
         for (int e = B.inc_start[i] + lane; e < e1; e += BT) {
-            const Imp q = B.imp[e];
-            accL = accL + f3(q.a);
-            accA = accA + make_float3(q.a.w, q.b.x, q.b.y);
+            // a share is read once, by its body
+            const float4 qa = __ldcs(&B.imp[e].a);
+            const float4 qb = __ldcs(&B.imp[e].b);
+            accL = accL + f3(qa);
+            accA = accA + make_float3(qa.w, qb.x, qb.y);
         }
         const int g1 = B.geo_start[p][i + 1];
         int k = B.geo_start[p][i] + lane;
@@ -552,7 +557,7 @@ static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int it
 
 static void sweep_dispatch(const SimParams& P, const DevBuf& B, int parity, int it, int nact, bool update,
                            cudaStream_t s) {
-    switch (P.lanes > 0 ? P.lanes : 2) {
+    switch (P.lanes > 0 && P.lanes <= 8 ? P.lanes : 2) {
         case 1: sweep_launch<1>(P, B, parity, it, nact, update, s); break;
         case 2: sweep_launch<2>(P, B, parity, it, nact, update, s); break;
         case 8: sweep_launch<8>(P, B, parity, it, nact, update, s); break;
@@ -568,7 +573,7 @@ int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
 }
 
 int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int nact, cudaStream_t s) {
-    if (P.lanes > 0) {   // single-kernel sweep, T threads per body
+    if (P.lanes > 0 && P.lanes <= 8) {   // single-kernel sweep, T threads per body
         sweep_dispatch(P, B, parity, it, nact, true, s);
         return 1;
     }

@@ -74,8 +74,9 @@ __global__ void __launch_bounds__(BP_T) k_cell_fill(SimParams P, DevBuf B) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     int c = B.body_cell[i];
-    int k = atomicAdd(&B.cell_fill[c], 1);
-    B.cell_body[B.cell_start[c] + k] = i;
+    int k = B.cell_start[c] + atomicAdd(&B.cell_fill[c], 1);
+    B.cell_body[k] = i;
+    B.cell_pos[k] = B.posr[i];   // candidates are read in cell order, without the slot hop
 }
 
 // ---------------------------------------------------------------------------
@@ -114,43 +115,57 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
         }
         int cx, cy, cz;
         cell_of(g, pi, cx, cy, cz);
-        const int z0 = max(cz - 1, 0), z1 = min(cz + 1, g.nz - 1);
-        const int y0 = max(cy - 1, 0), y1 = min(cy + 1, g.ny - 1);
         const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
-        for (int z = z0; z <= z1; ++z)
-            for (int y = y0; y <= y1; ++y) {
+        // the candidate ranges of the 3 x 3 rows of cells (z outer, y inner),
+        // all loaded at once; out-of-grid rows are empty
+        int st[9], pre[10];
+        pre[0] = 0;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            const int z = cz + r / 3 - 1, y = cy + r % 3 - 1;
+            int a = 0, b = 0;
+            if (z >= 0 && z < g.nz && y >= 0 && y < g.ny) {
                 const int row = g.offset + g.nx * (y + g.ny * z);
-                const int s = B.cell_start[row + x0], e = B.cell_start[row + x1 + 1];
-                for (int base = s; base < e; base += PT) {
-                    const int k = base + lane;
-                    bool hit = false;
-                    int j = 0, idj = 0;
-                    if (k < e) {
-                        j = B.cell_body[k];
-                        if (j != i) {
-                            const float4 pj = B.posr[j];
-                            const float R = pi.w + pj.w + P.tol;
-                            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                            if (dx * dx + dy * dy + dz * dz < R * R) {
-                                idj = B.id[j];
-                                // same level: the lower id owns the pair
-                                if (!(l == li && idj < idi)) hit = exact_pair(xi, B.pos[j]);
-                            }
-                        }
+                a = B.cell_start[row + x0];
+                b = B.cell_start[row + x1 + 1];
+            }
+            st[r] = a;
+            pre[r + 1] = pre[r] + (b - a);
+        }
+        // the rows' candidates as one list, shared out over the lanes in order
+        for (int base = 0; base < pre[9]; base += PT) {
+            const int t = base + lane;
+            bool hit = false;
+            int j = 0, idj = 0;
+            if (t < pre[9]) {
+                int k = st[0] + t;
+#pragma unroll
+                for (int r = 1; r < 9; ++r)
+                    if (t >= pre[r]) k = st[r] + (t - pre[r]);
+                const float4 pj = B.cell_pos[k];
+                const float R = pi.w + pj.w + P.tol;
+                const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                if (dx * dx + dy * dy + dz * dz < R * R) {
+                    j = B.cell_body[k];
+                    if (j != i) {
+                        idj = B.id[j];
+                        // same level: the lower id owns the pair
+                        if (!(l == li && idj < idi)) hit = exact_pair(xi, B.pos[j]);
                     }
-                    const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & 0xffu;
-                    if (hit) {
-                        const int q = nown + __popc(bal & below);
-                        if (q < DEM_MAX_OWN) {
-                            own[q] = make_int2(j, idj);
-                            atomicAdd(&B.in_cnt[j], 1);
-                        } else {
-                            overflow = true;
-                        }
-                    }
-                    nown += __popc(bal);
                 }
             }
+            const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & 0xffu;
+            if (hit) {
+                const int q = nown + __popc(bal & below);
+                if (q < DEM_MAX_OWN) {
+                    own[q] = make_int2(j, idj);
+                    atomicAdd(&B.in_cnt[j], 1);
+                } else {
+                    overflow = true;
+                }
+            }
+            nown += __popc(bal);
+        }
     }
     int ngeo = 0;
     int* gl = B.tmp_geo + (size_t)i * DEM_MAX_GEO;

@@ -104,7 +104,8 @@ struct DevBuf {
     int* cell_cnt;      // [n_cells + 1]
     int* cell_start;    // [n_cells + 1]
     int* cell_fill;     // [n_cells]
-    int* cell_body;     // [n]
+    int* cell_body;     // [n] slot of the particle in each cell position
+    float4* cell_pos;   // [n] its FP32 centre and radius, in cell order
     // per-body candidate lists of the current step
     int2* tmp_own;      // [n * DEM_MAX_OWN] (other slot, other stable id)
     int* tmp_geo;       // [n * DEM_MAX_GEO] primitive index

@@ -14,6 +14,10 @@ Parity status per function (what pins it is in tests/test_oracle_*.py):
   Jacobi sweep                pinned: converges to the MCP solution found by an
                               independent projected Gauss-Seidel on tiny cases
   step-size / iteration rules pinned: Table 3 of the paper
+  load-driven plate groups    pinned: free fall under load equals the discrete
+                              sum of the step; a loaded plate on a sphere on a
+                              floor reaches the Hertz static overlaps; particle
+                              plus plate momentum changes by exactly F t
   gradient (torch_step.py)    pinned: its FP64 forward equals oracle.c step by
                               step; its autograd gradient with respect to
                               (k_n scale, mu_t, mu_r) equals central finite

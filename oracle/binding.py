@@ -132,6 +132,8 @@ def load():
         lib.orc_get_contacts.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp]
         lib.orc_set_warmstart.argtypes = [vp, C.c_int64, i32, i32, d]
         lib.orc_threads.restype = C.c_int
+        lib.orc_set_load.restype = C.c_int
+        lib.orc_set_load.argtypes = [vp, C.c_int32, i32, C.c_double, d, C.c_int32]
         _lib = lib
     return _lib
 
@@ -225,6 +227,12 @@ class Oracle:
         lam = np.zeros((m, 7)); dl = np.zeros(m); nn = np.zeros((m, 3))
         self.lib.orc_get_contacts(self.h, m, _ptr(a), _ptr(b), _ptr(lam), _ptr(dl), _ptr(nn))
         return a, b, lam, dl, nn
+
+    def set_load(self, geoms, mass, force, dof=4):
+        """Bind primitives into one load-driven rigid group (orc_set_load)."""
+        g = np.ascontiguousarray(geoms, np.int32)
+        if self.lib.orc_set_load(self.h, len(g), g, float(mass), np.asarray(force, np.float64), int(dof)) != 0:
+            raise ValueError("orc_set_load rejected its arguments")
 
     def set_warmstart(self, key_a, key_b, lam7):
         ka = np.ascontiguousarray(key_a, np.int32); kb = np.ascontiguousarray(key_b, np.int32)

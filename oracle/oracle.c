@@ -241,6 +241,8 @@ typedef struct {
     double t1[3], t2[3];    /* tangent basis */
     double Ga[6][6], Gb[6][6]; /* rows: normal, t1, t2, roll x, roll y, roll z; cols: linear, angular */
     double known[6];        /* G_b (v_g, w_g) for kinematic geometry */
+    double known_ang[6];    /* its angular part G_b (0, w_g) */
+    int grp;                /* load-driven group of the primitive, or -1 */
     double sig[6], rhs[6];
     double Dn_inv, Dt_inv[2][2], Dr_inv[3][3];
     double mu_t, mu_r_reff;
@@ -260,6 +262,14 @@ struct orc_sim {
     ws_entry* ws;
     int64_t nws;
     double* gforce; /* 6 per geometry */
+    /* load-driven rigid groups of primitives (orc_set_load) */
+    int32_t ngrp;
+    int32_t* gbody;   /* per primitive: its group, or -1 (kinematic) */
+    struct {
+        double mass, force[3];
+        int32_t dof;    /* bit k: axis k is dynamic */
+        double v[3];    /* velocity of the group's primitives */
+    } grp[ORC_MAX_GROUPS];
 };
 
 int orc_threads(void) {
@@ -302,13 +312,34 @@ orc_sim* orc_create(const orc_params* p, int32_t n, const double* x, const doubl
     s->g = (orc_geom*)calloc(ng ? ng : 1, sizeof(orc_geom));
     if (ng) memcpy(s->g, g, (size_t)ng * sizeof(orc_geom));
     s->gforce = (double*)calloc(6 * (size_t)(ng ? ng : 1), sizeof(double));
+    s->gbody = (int32_t*)malloc((size_t)(ng ? ng : 1) * sizeof(int32_t));
+    for (int32_t k = 0; k < ng; ++k) s->gbody[k] = -1;
     return s;
+}
+
+int orc_set_load(orc_sim* s, int32_t count, const int32_t* geoms, double mass, const double force[3],
+                 int32_t dof) {
+    if (count < 1 || !(mass > 0.0) || dof <= 0 || dof > 7 || s->ngrp >= ORC_MAX_GROUPS) return -1;
+    for (int32_t k = 0; k < count; ++k)
+        if (geoms[k] < 0 || geoms[k] >= s->ng || s->gbody[geoms[k]] >= 0) return -1;
+    const int32_t q = s->ngrp++;
+    s->grp[q].mass = mass;
+    s->grp[q].dof = dof;
+    for (int a = 0; a < 3; ++a) {
+        s->grp[q].force[a] = force[a];
+        s->grp[q].v[a] = s->g[geoms[0]].v[a];
+    }
+    for (int32_t k = 0; k < count; ++k) {
+        s->gbody[geoms[k]] = q;
+        for (int a = 0; a < 3; ++a) s->g[geoms[k]].v[a] = s->grp[q].v[a];
+    }
+    return 0;
 }
 
 void orc_destroy(orc_sim* s) {
     if (!s) return;
     free(s->x); free(s->r); free(s->v); free(s->w); free(s->inv_m); free(s->inv_I);
-    free(s->id); free(s->g); free(s->c); free(s->ws); free(s->gforce);
+    free(s->id); free(s->g); free(s->c); free(s->ws); free(s->gforce); free(s->gbody);
     free(s);
 }
 
@@ -323,7 +354,17 @@ void orc_set_state(orc_sim* s, const double* x, const double* v, const double* w
     if (w) memcpy(s->w, w, 3 * (size_t)s->n * sizeof(double));
 }
 void orc_set_geom_velocity(orc_sim* s, int32_t g, const double v[3], const double w[3]) {
-    for (int k = 0; k < 3; ++k) { s->g[g].v[k] = v[k]; s->g[g].w[k] = w[k]; }
+    const int32_t q = s->gbody[g];
+    if (q < 0) {
+        for (int k = 0; k < 3; ++k) { s->g[g].v[k] = v[k]; s->g[g].w[k] = w[k]; }
+        return;
+    }
+    /* a group member: the prescribed axes of the whole group */
+    for (int k = 0; k < 3; ++k)
+        if (!(s->grp[q].dof >> k & 1)) s->grp[q].v[k] = v[k];
+    for (int32_t m = 0; m < s->ng; ++m)
+        if (s->gbody[m] == q)
+            for (int k = 0; k < 3; ++k) { s->g[m].v[k] = s->grp[q].v[k]; s->g[m].w[k] = w[k]; }
 }
 void orc_get_geom(const orc_sim* s, int32_t g, orc_geom* out) { *out = s->g[g]; }
 void orc_get_geom_force(const orc_sim* s, int32_t g, double f[3], double t[3]) {
@@ -442,6 +483,11 @@ static void step_once(orc_sim* s) {
         if (raw.v[k].b >= 0) cnt[raw.v[k].b]++;
     }
 
+    /* contacts per load-driven group: its split mass M / n_q */
+    int32_t ncg[ORC_MAX_GROUPS] = {0};
+    for (int64_t k = 0; k < raw.n; ++k)
+        if (raw.v[k].b < 0 && s->gbody[-raw.v[k].b - 1] >= 0) ncg[s->gbody[-raw.v[k].b - 1]]++;
+
     /* SPOOK constants (Lacoursiere 2007), d = tau/dt */
     const double Ups = 1.0 / (1.0 + 4.0 * P->damp_steps);
 
@@ -503,9 +549,12 @@ static void step_once(orc_sim* s) {
             c->Ga[3 + q][3 + q] = 1.0;
             c->Gb[3 + q][3 + q] = -1.0;
         }
+        c->grp = geo ? s->gbody[-c->b - 1] : -1;
         if (geo) {
-            for (int rrow = 0; rrow < 6; ++rrow)
-                c->known[rrow] = dot3(c->Gb[rrow], vb_lin) + dot3(&c->Gb[rrow][3], vb_ang);
+            for (int rrow = 0; rrow < 6; ++rrow) {
+                c->known_ang[rrow] = dot3(&c->Gb[rrow][3], vb_ang);
+                c->known[rrow] = dot3(c->Gb[rrow], vb_lin) + c->known_ang[rrow];
+            }
         }
         /* Hertz mapping: g = -delta^{e_H}, eps = e_H / k_n, k_n = E* sqrt(d*)/3.
          * The row is written for the physical normal impulse: the Hertz
@@ -531,12 +580,18 @@ static void step_once(orc_sim* s) {
         const double ima = cnt[a] * s->inv_m[a], iIa = cnt[a] * s->inv_I[a];
         const double imb = c->b >= 0 ? cnt[c->b] * s->inv_m[c->b] : 0.0;
         const double iIb = c->b >= 0 ? cnt[c->b] * s->inv_I[c->b] : 0.0;
+        /* inverse (split) mass of side b per axis: a particle's, a load-driven
+         * group's along its dynamic axes, zero for kinematic geometry */
+        double imb3[3] = {imb, imb, imb};
+        if (c->grp >= 0)
+            for (int q = 0; q < 3; ++q)
+                imb3[q] = (s->grp[c->grp].dof >> q & 1) ? ncg[c->grp] / s->grp[c->grp].mass : 0.0;
         for (int i = 0; i < 6; ++i)
             for (int j = 0; j < 6; ++j) {
                 double acc = 0.0;
                 for (int q = 0; q < 3; ++q) {
                     acc += c->Ga[i][q] * c->Ga[j][q] * ima + c->Ga[i][3 + q] * c->Ga[j][3 + q] * iIa;
-                    acc += c->Gb[i][q] * c->Gb[j][q] * imb + c->Gb[i][3 + q] * c->Gb[j][3 + q] * iIb;
+                    acc += c->Gb[i][q] * c->Gb[j][q] * imb3[q] + c->Gb[i][3 + q] * c->Gb[j][3 + q] * iIb;
                 }
                 D[i][j] = acc + (i == j ? c->sig[i] : 0.0);
             }
@@ -580,6 +635,31 @@ static void step_once(orc_sim* s) {
     for (int32_t i = 0; i < n; ++i)
         for (int q = 0; q < 3; ++q) vs[3 * i + q] = s->v[3 * i + q] + (s->inv_m[i] > 0.0 ? h * P->gravity[q] : 0.0);
 
+    /* load-driven groups: free velocity v_q* = v_q + dt F / M along the dynamic
+     * axes, current iterate vg */
+    double vgs[ORC_MAX_GROUPS][3], vg[ORC_MAX_GROUPS][3];
+    for (int32_t q = 0; q < s->ngrp; ++q)
+        for (int a = 0; a < 3; ++a) {
+            const int dyn = s->grp[q].dof >> a & 1;
+            vgs[q][a] = s->grp[q].v[a] + (dyn ? h * s->grp[q].force[a] / s->grp[q].mass : 0.0);
+            vg[q][a] = vgs[q][a];
+        }
+    /* v_q = v_q* + M^-1 sum over the group's contacts of the linear part of
+     * G_b^T lambda, along the dynamic axes; summed in contact order */
+    #define GROUP_UPDATE()                                                         \
+    for (int32_t q = 0; q < s->ngrp; ++q) {                                        \
+        double accg[3] = {0, 0, 0};                                                \
+        for (int64_t k = 0; k < s->nc; ++k) {                                      \
+            const contact* c = &s->c[k];                                           \
+            if (c->grp != q) continue;                                             \
+            double tmp[6] = {0, 0, 0, 0, 0, 0};                                    \
+            add_GT((double(*)[6])c->Gb, c->lam, tmp);                              \
+            for (int a = 0; a < 3; ++a) accg[a] += tmp[a];                         \
+        }                                                                          \
+        for (int a = 0; a < 3; ++a)                                                \
+            vg[q][a] = vgs[q][a] + ((s->grp[q].dof >> a & 1) ? accg[a] / s->grp[q].mass : 0.0); \
+    }
+
     /* v = v* + M^-1 sum_c G_c^T lambda_c */
     #define BODY_UPDATE()                                                          \
     _Pragma("omp parallel for schedule(static)")                                   \
@@ -595,6 +675,7 @@ static void step_once(orc_sim* s) {
         }                                                                          \
     }
     BODY_UPDATE();
+    GROUP_UPDATE();
 
     /* 3. N_it projected Jacobi sweeps */
     for (int32_t it = 0; it < P->n_it; ++it) {
@@ -605,6 +686,7 @@ static void step_once(orc_sim* s) {
             for (int row = 0; row < 6; ++row) {
                 double gv = dot3(c->Ga[row], &vv[3 * c->a]) + dot3(&c->Ga[row][3], &ww[3 * c->a]);
                 if (c->b >= 0) gv += dot3(c->Gb[row], &vv[3 * c->b]) + dot3(&c->Gb[row][3], &ww[3 * c->b]);
+                else if (c->grp >= 0) gv += dot3(c->Gb[row], vg[c->grp]) + c->known_ang[row];
                 else gv += c->known[row];
                 wres[row] = gv + c->sig[row] * c->lam[row] - c->rhs[row];
             }
@@ -631,8 +713,16 @@ static void step_once(orc_sim* s) {
         }
         for (int64_t k = 0; k < s->nc; ++k) memcpy(s->c[k].lam, s->c[k].lam_new, 6 * sizeof(double));
         BODY_UPDATE();
+        GROUP_UPDATE();
     }
     #undef BODY_UPDATE
+    #undef GROUP_UPDATE
+    /* the groups' new velocities move their primitives */
+    for (int32_t q = 0; q < s->ngrp; ++q)
+        for (int a = 0; a < 3; ++a) s->grp[q].v[a] = vg[q][a];
+    for (int32_t gi = 0; gi < s->ng; ++gi)
+        if (s->gbody[gi] >= 0)
+            for (int a = 0; a < 3; ++a) s->g[gi].v[a] = vg[s->gbody[gi]][a];
 
     /* 4. SPOOK position update with the new velocity */
     for (int32_t i = 0; i < n; ++i)

@@ -33,6 +33,7 @@ extern "C" {
 #endif
 
 enum { ORC_PLANE = 0, ORC_BOX = 1, ORC_CYLINDER = 2 };
+enum { ORC_MAX_GROUPS = 16 };
 
 typedef struct orc_params {
     double rho;          /* particle density [kg/m^3] (Sec. 3.1) */
@@ -75,6 +76,16 @@ orc_sim* orc_create(const orc_params* p, int32_t n, const double* x, const doubl
                     const double* inv_m, const double* inv_I,
                     int32_t ng, const orc_geom* g);
 void orc_destroy(orc_sim* s);
+/* Load-driven rigid group: the listed primitives translate together as one
+ * body of the given mass under a constant external force [N] along the axes
+ * whose bit is set in dof (bit 0 x, 1 y, 2 z); along the other axes they keep
+ * their prescribed velocity; they do not rotate dynamically.  The group's
+ * velocity is an unknown of every step's solve like a particle's (a dynamic
+ * motor-free plate, the paper's plate under a normal load F_N, Sec. 3.3).
+ * The group starts with the velocity of its first member.  Returns 0, or -1
+ * for bad arguments or a primitive already in a group. */
+int orc_set_load(orc_sim* s, int32_t count, const int32_t* geoms, double mass, const double force[3],
+                 int32_t dof);
 int orc_step(orc_sim* s, int32_t nsteps);
 void orc_get_state(const orc_sim* s, double* x, double* v, double* w);
 void orc_set_state(orc_sim* s, const double* x, const double* v, const double* w);

@@ -198,6 +198,20 @@ dem_status dem_read_timing(dem_bed* bed, double* step_ms, double* jacobi_ms, int
  * (the test phase starts here).  Synchronises; the per-step graphs are rebuilt. */
 dem_status dem_set_params(dem_bed* bed, const dem_bed_desc* desc);
 
+/* Load-driven plate (Sec. 3.3: the plate under a normal load F_N).  The listed
+ * primitives (count of them, one bed) become one rigid group that translates
+ * along the axes whose bit is set in dof (bit 0 x, 1 y, 2 z) as a body of the
+ * given mass [kg] under the constant external force [N] (gravity is not added:
+ * include M g in force if wanted).  Its velocity along those axes is an unknown
+ * of every step's Jacobi solve, with split mass M / (contacts of the group);
+ * along the other axes the group keeps the motor velocity of dem_apply_plate_velocity
+ * (which, on a member, sets the whole group's motor axes).  The group starts
+ * with the velocity of geoms[0]; it does not rotate dynamically.  Up to 16
+ * groups per object.  DEM_ERR_ARG for bad arguments or a primitive already in a
+ * group.  Synchronises. */
+dem_status dem_apply_plate_load(dem_bed* bed, const int32_t* geoms, int32_t count, double mass,
+                                const double force[3], int32_t dof);
+
 /* ---- differentiation (reverse mode) -------------------------------------
  * Gradients of J = sum_t sum_g dJ_dF[t][g] . F_t,g, a linear functional of
  * the force on every primitive in every step, with respect to the scale s_k of

@@ -100,6 +100,7 @@ struct Checkpoint {
     float4* glamW = nullptr;
     float* c_delta = nullptr;   // overlaps of that step (read-back)
     float* g_delta = nullptr;
+    GroupDev* grp = nullptr;    // load-driven groups (velocities)
     void* mem = nullptr;
     size_t bytes = 0;
 };
@@ -736,7 +737,7 @@ static dem_status save_checkpoint(dem_bed* b, Checkpoint& K) {
         c.take(K.pos, n); c.take(K.posr, n); c.take(K.vw0, n); c.take(K.id, n); c.take(K.lvl, n);
         c.take(K.geom, ng); c.take(K.own_start, n + 1); c.take(K.geo_start, n + 1);
         c.take(K.c_key, nc); c.take(K.lamW, 2 * (size_t)nc); c.take(K.g_key, ngc); c.take(K.glamW, 2 * (size_t)ngc);
-        c.take(K.c_delta, nc); c.take(K.g_delta, ngc);
+        c.take(K.c_delta, nc); c.take(K.g_delta, ngc); c.take(K.grp, DEM_MAX_GROUPS);
     });
     if (st != DEM_OK) return st;
     cudaStream_t s = b->stream;
@@ -757,6 +758,7 @@ static dem_status save_checkpoint(dem_bed* b, Checkpoint& K) {
     DEM_CK(cp(K.glamW, B.glamW[q], 2 * (size_t)ngc * sizeof(float4)));
     DEM_CK(cp(K.c_delta, B.c_delta, nc * sizeof(float)));
     DEM_CK(cp(K.g_delta, B.g_delta, ngc * sizeof(float)));
+    DEM_CK(cp(K.grp, B.grp, DEM_MAX_GROUPS * sizeof(GroupDev)));
     return DEM_OK;
 }
 
@@ -784,6 +786,7 @@ static dem_status restore_checkpoint(dem_bed* b, const Checkpoint& K) {
     DEM_CK(cp(B.glamW[q], K.glamW, 2 * (size_t)K.ngc_prev * sizeof(float4)));
     DEM_CK(cp(B.c_delta, K.c_delta, K.nc_prev * sizeof(float)));
     DEM_CK(cp(B.g_delta, K.g_delta, K.ngc_prev * sizeof(float)));
+    DEM_CK(cp(B.grp, K.grp, DEM_MAX_GROUPS * sizeof(GroupDev)));
     DEM_CK(cudaMemsetAsync(B.resorted, 0, sizeof(int), s));
     return DEM_OK;
 }
@@ -898,6 +901,8 @@ static dem_status check_supported(dem_bed* b) {
         DEM_CK(cudaStreamSynchronize(b->stream));
     }
     for (int g = 0; g < P.ng; ++g) {
+        if (hg[g].grp >= 0)
+            return dem_fail(DEM_ERR_ARG, "the adjoint does not support load-driven primitives (primitive %d)", g);
         if (hg[g].type != DEM_GEOM_PLANE)
             return dem_fail(DEM_ERR_ARG, "the adjoint supports plane primitives only (primitive %d)", g);
         if (hg[g].w[0] != 0.0 || hg[g].w[1] != 0.0 || hg[g].w[2] != 0.0)

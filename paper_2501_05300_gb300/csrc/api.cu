@@ -116,6 +116,24 @@ static double estar(double E1, double nu1, double E2, double nu2) {
 }
 
 static dem_status build_graphs(dem_bed* b);
+static dem_status rebuild_graphs(dem_bed* b);
+
+// motor velocity of a load-driven group: the prescribed axes of the group and of
+// every member (the dynamic axes keep their solved velocity)
+__global__ void k_group_motor(DevBuf B, int ng, int q, double vx, double vy, double vz, double wx, double wy,
+                              double wz) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    GroupDev& Q = B.grp[q];
+    const double v[3] = {vx, vy, vz}, w[3] = {wx, wy, wz};
+    for (int ax = 0; ax < 3; ++ax)
+        if (!(Q.dof >> ax & 1)) Q.v[ax] = v[ax];
+    for (int g = 0; g < ng; ++g)
+        if (B.geom[g].grp == q)
+            for (int ax = 0; ax < 3; ++ax) {
+                B.geom[g].v[ax] = Q.v[ax];
+                B.geom[g].w[ax] = w[ax];
+            }
+}
 
 // Height of the particle surface under each primitive: the highest top z + r
 // of the particles whose centre lies inside the primitive's footprint in x, y
@@ -219,6 +237,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     }
     b->resort_every = d->resort_every > 0 ? d->resort_every : 20;
     b->n_geom = (int)ng64;
+    b->geom_group.assign(std::max<int64_t>(ng64, 1), -1);
     b->nbeds = nbeds;
 
     // host copies of the inputs (they may live on the device)
@@ -479,6 +498,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     AL(B.glamA[0], GC); AL(B.glamA[1], GC); AL(B.glamB[0], GC); AL(B.glamB[1], GC);
     AL(B.glamW[0], 2 * GC); AL(B.glamW[1], 2 * GC);
     AL(B.geom, (size_t)std::max(P.ng, 1)); AL(B.gacc, 6 * (size_t)std::max(P.ng, 1));
+    AL(B.grp, DEM_MAX_GROUPS); AL(B.gcnt, DEM_MAX_GROUPS); AL(B.gimp, 9 * DEM_MAX_GROUPS);
     AL(B.key_a, N); AL(B.key_b, N); AL(B.val_a, N); AL(B.val_b, N);
     AL(B.hist, 256 * (size_t)nbr + 1);
     AL(B.t_pos, N); AL(B.t_vw, N); AL(B.t_id, N); AL(B.t_lvl, N);
@@ -515,6 +535,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
         o.Estar = (float)estar(d->E, d->nu, G.E, G.nu);
         o.mu_t = G.mu_t;
         o.mu_r = G.mu_r;
+        o.grp = -1;
         o.bound = (float)(G.type == DEM_GEOM_BOX ? std::sqrt(G.he[0] * G.he[0] + G.he[1] * G.he[1] + G.he[2] * G.he[2])
                                                  : std::sqrt(G.he[0] * G.he[0] + G.he[2] * G.he[2])) * 1.0001f;
     }
@@ -534,6 +555,9 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     CK(cudaMemsetAsync(B.err, 0, sizeof(int), s));
     CK(cudaMemsetAsync(B.resorted, 0, sizeof(int), s));
     CK(cudaMemsetAsync(B.gacc, 0, 6 * std::max(P.ng, 1) * sizeof(long long), s));
+    CK(cudaMemsetAsync(B.grp, 0, DEM_MAX_GROUPS * sizeof(GroupDev), s));
+    CK(cudaMemsetAsync(B.gcnt, 0, DEM_MAX_GROUPS * sizeof(int), s));
+    CK(cudaMemsetAsync(B.gimp, 0, 9 * DEM_MAX_GROUPS * sizeof(long long), s));
     CK(cudaStreamSynchronize(s));
 
     st = build_graphs(b);
@@ -586,6 +610,10 @@ static int body_pre(dem_bed* b, int p) {
     cudaMemsetAsync(B.in_cnt, 0, (N + 1) * sizeof(int), s);
     cudaMemsetAsync(B.in_fill, 0, (N + 1) * sizeof(int), s);
     cudaMemsetAsync(B.gacc, 0, 6 * std::max(P.ng, 1) * sizeof(long long), s);
+    if (P.n_groups > 0) {
+        cudaMemsetAsync(B.gcnt, 0, DEM_MAX_GROUPS * sizeof(int), s);
+        cudaMemsetAsync(B.gimp, 0, 9 * DEM_MAX_GROUPS * sizeof(long long), s);
+    }
     // per-level boxes start empty: lo = huge (bytes 0x7f), hi = -huge (bytes 0x80)
     cudaMemsetAsync(B.lvl_lo, 0x7f, 3 * (size_t)P.n_levels * sizeof(int), s);
     cudaMemsetAsync(B.lvl_hi, 0x80, 3 * (size_t)P.n_levels * sizeof(int), s);
@@ -738,10 +766,67 @@ extern "C" dem_status dem_apply_plate_velocity(dem_bed* b, int32_t g, const doub
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(v[k]) || !std::isfinite(w[k])) return fail(DEM_ERR_ARG, "non-finite velocity");
     CK(cudaSetDevice(b->dev));
+    if (b->geom_group[g] >= 0) {   // a load-driven group: its prescribed axes, all members
+        k_group_motor<<<1, 32, 0, b->stream>>>(b->B, b->P.ng, b->geom_group[g], v[0], v[1], v[2], w[0], w[1], w[2]);
+        CK(cudaGetLastError());
+        return DEM_OK;
+    }
     double vw[6] = {v[0], v[1], v[2], w[0], w[1], w[2]};
     // v and w are adjacent in GeomDev; a pageable source is staged before return
     CK(cudaMemcpyAsync(&b->B.geom[g].v[0], vw, 6 * sizeof(double), cudaMemcpyHostToDevice, b->stream));
     return DEM_OK;
+}
+
+// the primitives of one group: their bed's sweep count
+static int group_bed_nit(const dem_bed* b, int g) {
+    for (const LevelGrid& l : b->levels)
+        if (g >= l.g0 && g < l.g1) return l.nit;
+    return b->P.n_it;
+}
+
+extern "C" dem_status dem_apply_plate_load(dem_bed* b, const int32_t* geoms, int32_t count, double mass,
+                                           const double force[3], int32_t dof) {
+    g_err.clear();
+    if (!b || !geoms || !force) return fail(DEM_ERR_ARG, "NULL argument");
+    if (count < 1 || !(mass > 0.0) || !std::isfinite(mass) || dof < 1 || dof > 7)
+        return fail(DEM_ERR_ARG, "need count >= 1, mass > 0 and dof in 1..7");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(force[k])) return fail(DEM_ERR_ARG, "non-finite force");
+    if (b->P.n_groups >= DEM_MAX_GROUPS) return fail(DEM_ERR_ARG, "more than %d load-driven groups", DEM_MAX_GROUPS);
+    const int bed0 = group_bed_nit(b, geoms[0]);
+    for (int k = 0; k < count; ++k) {
+        const int g = geoms[k];
+        if (g < 0 || g >= b->n_geom) return fail(DEM_ERR_ARG, "geom %d out of range", g);
+        if (b->geom_group[g] >= 0) return fail(DEM_ERR_ARG, "geom %d already belongs to a group", g);
+        for (int m = 0; m < k; ++m)
+            if (geoms[m] == g) return fail(DEM_ERR_ARG, "geom %d listed twice", g);
+        if (group_bed_nit(b, g) != bed0) return fail(DEM_ERR_ARG, "a group's primitives must share one bed");
+    }
+    CK(cudaSetDevice(b->dev));
+    const int q = b->P.n_groups;
+    GeomDev G0;
+    CK(cudaMemcpyAsync(&G0, b->B.geom + geoms[0], sizeof G0, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    GroupDev Q;
+    memset(&Q, 0, sizeof Q);
+    for (int k = 0; k < 3; ++k) {
+        Q.v[k] = G0.v[k];
+        Q.force[k] = (float)force[k];
+    }
+    Q.inv_mass = (float)(1.0 / mass);
+    Q.dof = dof;
+    Q.nit = bed0;
+    CK(cudaMemcpyAsync(b->B.grp + q, &Q, sizeof Q, cudaMemcpyHostToDevice, b->stream));
+    for (int k = 0; k < count; ++k) {
+        const int g = geoms[k];
+        // members join with the group's velocity
+        CK(cudaMemcpyAsync(&b->B.geom[g].v[0], Q.v, 3 * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(&b->B.geom[g].grp, &q, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+        b->geom_group[g] = q;
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    b->P.n_groups = q + 1;
+    return rebuild_graphs(b);
 }
 
 static double z_bottom(const GeomDev& G) {
@@ -978,6 +1063,8 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
     }
     P.n_it = d->n_it;   // every bed now takes n_it sweeps
     P.nit_uniform = 1;
+    for (int q = 0; q < P.n_groups; ++q)
+        CK(cudaMemcpyAsync(&b->B.grp[q].nit, &P.n_it, sizeof(int), cudaMemcpyHostToDevice, b->stream));
     for (LevelGrid& g : b->levels) g.nit = d->n_it;
     b->n_active.assign(std::max(d->n_it, 1), P.n);
     P.dt = d->dt;

@@ -25,6 +25,7 @@ struct dem_bed {
     void* actx = nullptr;
     std::vector<void*> allocs;
     int n_geom = 0;
+    std::vector<int> geom_group;     // load-driven group of each primitive, or -1
     int nbeds = 1;
     std::vector<LevelGrid> levels;   // host copy of the level table
     std::vector<int> n_active;       // particles of beds still sweeping, per sweep

@@ -236,6 +236,8 @@ __global__ void __launch_bounds__(BP_T) k_contacts_build(SimParams P, DevBuf B, 
     for (int k = 0; k < ng; ++k) {
         if (gs + k >= gcap) { set_flag(B.err, DEM_FLAG_CAPACITY); break; }
         B.g_key[parity][gs + k] = gl[k];
+        const int q = B.geom[gl[k]].grp;
+        if (q >= 0) atomicAdd(&B.gcnt[q], 1);   // split mass of a load-driven group
     }
 }
 

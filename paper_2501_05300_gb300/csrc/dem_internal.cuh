@@ -24,6 +24,7 @@
 #define DEM_MAX_OWN 32   // sphere-sphere contacts one body may own per step
 #define DEM_MAX_GEO 8    // sphere-geometry contacts per body per step
 #define DEM_FIX_SCALE 17592186044416.0  // 2^44: fixed-point scale of geometry impulses [N s]
+#define DEM_MAX_GROUPS 16  // load-driven rigid groups of primitives
 
 enum { DEM_FLAG_CAPACITY = 1, DEM_FLAG_NONFINITE = 2 };
 
@@ -64,7 +65,19 @@ struct GeomDev {
     float Estar;        // effective modulus of the sphere-geometry pair
     float mu_t, mu_r;
     float bound;        // radius of a sphere around c holding the primitive (box, cylinder)
-    float pad;
+    int grp;            // load-driven rigid group the primitive belongs to, or -1
+};
+
+// A load-driven rigid group of primitives (a plate under a normal load): it
+// translates along its dynamic axes as one body of mass 1/inv_mass under a
+// constant force, its velocity an unknown of the Jacobi solve; along the other
+// axes it keeps its prescribed velocity.
+struct GroupDev {
+    double v[3];        // velocity at the start of the step (all members)
+    float force[3];     // external force [N]
+    float inv_mass;     // 1 / M
+    int dof;            // bit k: axis k is dynamic
+    int nit;            // Jacobi sweeps of the group's bed
 };
 
 struct SimParams {
@@ -81,6 +94,7 @@ struct SimParams {
     float tol;          // FP32 broad-phase tolerance [m], covers FP32 rounding of positions
     int lanes;          // sweep layout: 0 two-pass, else threads per body in one kernel
     int nit_uniform;    // 1 when every bed takes n_it sweeps
+    int n_groups;       // load-driven groups
 };
 
 // Device pointers of one bed.  The two warm-start generations (parity of the
@@ -139,6 +153,11 @@ struct DevBuf {
     // kinematic geometry and its force accumulators
     GeomDev* geom;      // [ng]
     long long* gacc;    // [6 ng] fixed-point impulse and angular impulse
+    // load-driven groups
+    GroupDev* grp;      // [DEM_MAX_GROUPS]
+    int* gcnt;          // [DEM_MAX_GROUPS] contacts of each group this step
+    long long* gimp;    // [3][DEM_MAX_GROUPS][3] fixed-point impulse on each group, per
+                        //   iterate k (buffer k % 3): read at sweep k, written at k - 1
     // re-sort scratch
     unsigned* key_a; unsigned* key_b;
     int* val_a; int* val_b;
@@ -202,6 +221,45 @@ static __device__ __forceinline__ int cell_coord(float x, float o, float inv, in
 }
 
 static __device__ __forceinline__ void set_flag(int* err, int bit) { atomicOr(err, bit); }
+
+// velocity of group q at Jacobi iterate k: v* + M^-1 (sum of the impulses of
+// iterate k on it) along the dynamic axes, v* = v + dt F / M
+static __device__ __forceinline__ void group_velocity_d(const SimParams& P, const DevBuf& B, int q, int k,
+                                                        double v[3]) {
+    const GroupDev& G = B.grp[q];
+    const long long* a = B.gimp + 3 * ((k % 3) * DEM_MAX_GROUPS + q);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        v[ax] = G.v[ax];
+        if (G.dof >> ax & 1)
+            v[ax] += (double)P.dt * G.force[ax] * G.inv_mass + G.inv_mass * ((double)a[ax] / DEM_FIX_SCALE);
+    }
+}
+
+static __device__ __forceinline__ float3 group_velocity(const SimParams& P, const DevBuf& B, int q, int k) {
+    double v[3];
+    group_velocity_d(P, B, q, k, v);
+    return make_float3((float)v[0], (float)v[1], (float)v[2]);
+}
+
+// clear the impulse sum of iterate it + 2 before sweep it + 1 writes it (sweep
+// it runs this from block 0; the sum was last read by sweep it - 1)
+static __device__ __forceinline__ void group_clear_ahead(const SimParams& P, const DevBuf& B, int it) {
+    if (blockIdx.x == 0 && (int)threadIdx.x < 3 * P.n_groups) {
+        const int q = threadIdx.x / 3;
+        if (it + 2 <= B.grp[q].nit) B.gimp[3 * (((it + 2) % 3) * DEM_MAX_GROUPS + q) + threadIdx.x % 3] = 0;
+    }
+}
+
+// add the impulse Pg of one contact on group q to iterate k's sum (fixed point:
+// the sum does not depend on the order of the additions)
+static __device__ __forceinline__ void group_add(const DevBuf& B, int q, int k, float3 Pg) {
+    unsigned long long* a = (unsigned long long*)(B.gimp + 3 * ((k % 3) * DEM_MAX_GROUPS + q));
+    const int dof = B.grp[q].dof;
+    if (dof & 1) atomicAdd(a, (unsigned long long)__double2ll_rn((double)Pg.x * DEM_FIX_SCALE));
+    if (dof & 2) atomicAdd(a + 1, (unsigned long long)__double2ll_rn((double)Pg.y * DEM_FIX_SCALE));
+    if (dof & 4) atomicAdd(a + 2, (unsigned long long)__double2ll_rn((double)Pg.z * DEM_FIX_SCALE));
+}
 
 // Jacobi sweeps per step of the bed of body i
 static __device__ __forceinline__ int body_nit(const SimParams& P, const DevBuf& B, int i) {

@@ -152,12 +152,32 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         const float ima = na * va.w, iIa = na * wa.w;
         const float Gv = dot(n, f3(va) - vgp);
         const RowC rc = spook_row(P, delta, kn, Gv, ima, la * la * iIa, iIa);
+        // side b's split inverse mass: zero for kinematic geometry; a load-driven
+        // group's M / n_q along its dynamic axes, which makes the tangential
+        // block of D anisotropic (full 2x2 inverse: i11, i12, i22)
+        float invDn = rc.invDn, i11 = rc.invDt, i12 = 0.f, i22 = rc.invDt;
+        if (G.grp >= 0) {
+            const GroupDev& Q = B.grp[G.grp];
+            const float imq = (float)B.gcnt[G.grp] * Q.inv_mass;
+            const float mx = (Q.dof & 1) ? imq : 0.f, my = (Q.dof & 2) ? imq : 0.f, mz = (Q.dof & 4) ? imq : 0.f;
+            float3 t1, t2;
+            tangent_basis(n, t1, t2);
+            invDn = 1.0f / (ima + (mx * n.x * n.x + my * n.y * n.y + mz * n.z * n.z) + rc.sig);
+            const float base = ima + la * la * iIa + P.eps_reg * rc.sig;
+            const float d11 = base + (mx * t1.x * t1.x + my * t1.y * t1.y + mz * t1.z * t1.z);
+            const float d22 = base + (mx * t2.x * t2.x + my * t2.y * t2.y + mz * t2.z * t2.z);
+            const float d12 = mx * t1.x * t2.x + my * t1.y * t2.y + mz * t1.z * t2.z;
+            const float idet = 1.0f / (d11 * d22 - d12 * d12);
+            i11 = d22 * idet;
+            i12 = -d12 * idet;
+            i22 = d11 * idet;
+        }
         float4* r = B.grec + 6 * (size_t)k;
-        r[0] = make_float4(n.x, n.y, n.z, rc.invDn);
-        r[1] = make_float4(rc.rhs, rc.sig, rc.invDt, rc.invDr);
+        r[0] = make_float4(n.x, n.y, n.z, invDn);
+        r[1] = make_float4(rc.rhs, rc.sig, i11, rc.invDr);
         r[2] = make_float4(la, G.mu_t, G.mu_r * ra, __int_as_float(g));
-        r[3] = make_float4(vgp.x, vgp.y, vgp.z, 0.f);
-        r[4] = make_float4(wg.x, wg.y, wg.z, 0.f);
+        r[3] = make_float4(vgp.x, vgp.y, vgp.z, i12);
+        r[4] = make_float4(wg.x, wg.y, wg.z, i22);
         r[5] = make_float4(lever.x, lever.y, lever.z, 0.f);
         B.g_delta[k] = delta;
         float4 l0 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -180,9 +200,13 @@ struct Upd {
     float3 pr, t1, t2;
 };
 
+// G2: the tangential block of D is a full 2x2 (i11 = r1.z, i12, i22), for the
+// contacts of a load-driven group; otherwise it is r1.z times the identity
+template <bool G2 = false>
 static __device__ __forceinline__ Upd contact_update(float4 r0, float4 r1, float la, float lb, float mu_t,
                                                      float mur, float4 l0, float2 l1, float3 dv,
-                                                     float3 wa, float3 wb, float eps_reg) {
+                                                     float3 wa, float3 wb, float eps_reg, float i12 = 0.f,
+                                                     float i22 = 0.f) {
     Upd u;
     const float3 n = f3(r0);
     const float sig = r1.y, sig_t = eps_reg * r1.y;
@@ -192,8 +216,15 @@ static __device__ __forceinline__ Upd contact_update(float4 r0, float4 r1, float
     // contact-point relative velocity: dv + w_a x (-l_a n) - w_b x (l_b n)
     const float3 uc = dv - cross(la * wa + lb * wb, n);
     tangent_basis(n, u.t1, u.t2);
-    float pt1 = l0.y - r1.z * (dot(uc, u.t1) + sig_t * l0.y);
-    float pt2 = l0.z - r1.z * (dot(uc, u.t2) + sig_t * l0.z);
+    float pt1, pt2;
+    if (G2) {
+        const float w1 = dot(uc, u.t1) + sig_t * l0.y, w2 = dot(uc, u.t2) + sig_t * l0.z;
+        pt1 = l0.y - (r1.z * w1 + i12 * w2);
+        pt2 = l0.z - (i12 * w1 + i22 * w2);
+    } else {
+        pt1 = l0.y - r1.z * (dot(uc, u.t1) + sig_t * l0.y);
+        pt2 = l0.z - r1.z * (dot(uc, u.t2) + sig_t * l0.z);
+    }
     const float bt = mu_t * u.pn;
     const float m2 = pt1 * pt1 + pt2 * pt2;
     if (m2 > bt * bt) {   // Coulomb disc (Eq. 6)
@@ -210,6 +241,24 @@ static __device__ __forceinline__ Upd contact_update(float4 r0, float4 r1, float
     const float q2 = dot(pr, pr);
     if (q2 > br * br) pr = (br * rsqrtf(q2)) * pr;
     u.pr = pr;
+    return u;
+}
+
+// Update of sphere-geometry contact k at sweep it from the body's iterate
+// (vi, wi); a load-driven group's contact takes the group's iterate and adds
+// its impulse to the group's sum for iterate it + 1.
+static __device__ __forceinline__ Upd geom_update(const SimParams& P, const DevBuf& B, const float4* r, int k,
+                                                  int src, int it, float3 vi, float3 wi) {
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+    const float4 l0 = B.glamA[src][k];
+    const float2 l1 = B.glamB[src][k];
+    const int q = B.geom[__float_as_int(r2.w)].grp;
+    if (q < 0) return contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4), P.eps_reg);
+    const float3 vgp = group_velocity(P, B, q, it) + cross(f3(r4), f3(r[5]));
+    const Upd u = contact_update<true>(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - vgp, wi, f3(r4), P.eps_reg,
+                                       r3.w, r4.w);
+    const float3 n = f3(r0);
+    group_add(B, q, it + 1, (-1.0f) * (u.pn * n + u.pt1 * u.t1 + u.pt2 * u.t2));
     return u;
 }
 
@@ -235,6 +284,7 @@ static __device__ __forceinline__ float sub_sum(float v) {
 template <int T, bool UPDATE>
 __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, int it) {
     if (*B.err) return;
+    if (UPDATE) group_clear_ahead(P, B, it);
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gt / T, lane = gt % T;
     bool active = i < P.n;
@@ -293,8 +343,7 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
             const float3 n = f3(r0);
             Upd u;
             if (UPDATE) {
-                const float4 r1 = r[1], r3 = r[3], r4 = r[4];
-                u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4), P.eps_reg);
+                u = geom_update(P, B, r, k, src, it, vi, wi);
                 if (!last) {
                     B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
                     B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
@@ -302,6 +351,9 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
             } else {
                 tangent_basis(n, u.t1, u.t2);
                 u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
+                const int q = B.geom[__float_as_int(r2.w)].grp;
+                if (q >= 0)   // the warm start's impulse on a load-driven group: iterate 0
+                    group_add(B, q, 0, (-1.0f) * (u.pn * n + u.pt1 * u.t1 + u.pt2 * u.t2));
             }
             if (last) write_world(B.glamW[p], k, n, u);
             add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
@@ -372,6 +424,16 @@ __global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p
         for (int t = threadIdx.x; t < 6 * P.ng; t += blockDim.x)
             if (sacc[t] != 0) atomicAdd((unsigned long long*)&B.gacc[t], (unsigned long long)sacc[t]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // load-driven groups: the solved velocity of the final iterate moves
+        // the members along the dynamic axes
+        for (int q = 0; q < P.n_groups; ++q) {
+            double vf[3];
+            group_velocity_d(P, B, q, B.grp[q].nit, vf);
+            for (int ax = 0; ax < 3; ++ax) B.grp[q].v[ax] = vf[ax];
+        }
+        for (int g = 0; g < P.ng; ++g)
+            if (B.geom[g].grp >= 0)
+                for (int ax = 0; ax < 3; ++ax) B.geom[g].v[ax] = B.grp[B.geom[g].grp].v[ax];
         // kinematic primitives: translate with v, rotate with w (Rodrigues)
         const double h = (double)P.dt;
         for (int g = 0; g < P.ng; ++g) {
@@ -423,6 +485,7 @@ __global__ void __launch_bounds__(SV_T, 12) k_contact_pass(SimParams P, DevBuf B
     pdl_wait();
     pdl_trigger();
     if (*B.err) return;
+    group_clear_ahead(P, B, it);
     const int src = it & 1, dst = src ^ 1;
     // contacts are stored in owner order: those of the active prefix come first
     const int nc = min(B.own_start[p][nact], P.max_contacts);
@@ -490,12 +553,9 @@ __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p
             const float3 vi = f3(me.v), wi = f3(me.w);
             for (; k < g1; k += BT) {
                 const float4* r = B.grec + 6 * (size_t)k;
-                const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
-                const float4 l0 = B.glamA[src][k];
-                const float2 l1 = B.glamB[src][k];
+                const float4 r0 = r[0], r2 = r[2];
                 const float3 n = f3(r0);
-                const Upd u = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4),
-                                             P.eps_reg);
+                const Upd u = geom_update(P, B, r, k, src, it, vi, wi);
                 if (last) {
                     write_world(B.glamW[p], k, n, u);
                 } else {

@@ -148,12 +148,19 @@ def settle_and_place(dem, spec, settle_steps, lanes):
     return b, top
 
 
+# shear plate: 10 kPa on 0.3 x 0.3 m (the plate's own weight included), plate
+# and grousers of 8 kg
+FINE_LOAD = 10e3 * 0.3 * 0.3
+FINE_PLATE_MASS = 8.0
+
+
 def settle_fine(dem, lx, ly, settle_steps, lanes, nit):
     """The homogeneous fine bed (r = 2.5 mm, 10% spread, depth 0.25 m) on an
     lx x ly footprint, settled like the refined bed (generation friction of
     Sec. 3.1, dt 2e-4, plate lifted clear), switched to the test settings
     (dt 1e-5, mu_t 0.5, mu_r 0.02, N_it = nit), with the 0.3 x 0.3 m plate and
-    its three grousers lowered until the grouser tips touch the surface."""
+    its three grousers lowered until the grouser tips touch the surface, then
+    made one load-driven body under a 10 kPa normal load."""
     spec = beds.fine_shear_bed(lx, ly)
     m = spec.material
     geoms = list(spec.geoms)
@@ -178,6 +185,9 @@ def settle_fine(dem, lx, ly, settle_steps, lanes, nit):
     bed.step(1)
     for gi in spec.plate_parts:
         bed.apply_plate_velocity(gi, (0.0, 0.0, 0.0))
+    # from here the plate and grousers are one body under the normal load
+    # (vertical dynamics), dragged by their motor along x
+    bed.apply_plate_load(list(spec.plate_parts), FINE_PLATE_MASS, (0.0, 0.0, -FINE_LOAD), dof=4)
     return bed, spec
 
 
@@ -211,13 +221,17 @@ def run_fine(args):
     contacts = info.contacts + info.geom_contacts
     ms = step_ms / ts
     sweep_ms = jac_ms / (ts * nit)
+    fx = sum(bed.read_forces(gi)[0][0] for gi in spec.plate_parts)
+    fz = sum(bed.read_forces(gi)[0][2] for gi in spec.plate_parts)
+    zs = bed.read_geom(spec.plate).c[2]
     alg = BYTES_PER_CONTACT * contacts + BYTES_PER_BODY * info.n
     peak = measured_peaks().get("hbm_gbs", 6800.0)
     bed.close()
     return dict(value=info.n / (ms * 1e-3), ms_per_step=ms, n=info.n, contacts=contacts, n_it=nit,
                 contacts_at_start=start.contacts + start.geom_contacts, footprint=(lx, ly),
                 sweep_us=sweep_ms * 1e3, achieved=alg / (sweep_ms * 1e-3) / 1e9, peak=peak,
-                lanes=info.lanes, launches=args.steps * info.kernels_per_step, clocks=clk.summary())
+                lanes=info.lanes, launches=args.steps * info.kernels_per_step, clocks=clk.summary(),
+                plate_force_N=[fx, fz], plate_z=zs)
 
 
 def run_gpu(args, rank, world):
@@ -472,6 +486,27 @@ def prepare_triaxial(dem, lanes=0, n=TRIAX_N, seed=2505, max_steps=8000):
     return bed, dict(consolidation_steps=steps, n_it=nit, height=h, stress=sig)
 
 
+def oracle_gradient_sample(n=5000, squeeze=0.095, steps=1):
+    """Time the FP64 gradient oracle (autograd through oracle/torch_step.py,
+    as it stands) on a bounded sample of the triaxial workload: a 5,000-sphere
+    cell whose lattice is squeezed to ~3 contacts per particle, one step with
+    N_it = 172, the same objective."""
+    import torch
+    import oracle
+    from oracle import torch_step as ts
+    b = beds.triaxial_cell(n, squeeze=squeeze, v_top=-TRIAX_RATE * 0.2)
+    geoms = [oracle.Geom(g.type, g.c, g.R, g.he, g.v, g.w, g.E, g.nu, g.mu_t, g.mu_r) for g in b.geoms]
+    p = oracle.OracleParams(rho=b.material.rho, n_it=172, gravity=(0.0, 0.0, 0.0), dt=DT)
+    W = np.zeros((6, 3))
+    W[beds.PLATEN, 2] = 1.0
+    contacts = len(oracle.detect(b.x, b.r.astype(np.float64), np.arange(b.n, dtype=np.int32), geoms)[0])
+    t0 = time.perf_counter()
+    ts.gradient(p, b.x, b.r.astype(np.float64), np.zeros_like(b.x), np.zeros_like(b.x), geoms,
+                (1.0, 0.5, 0.02), steps, W)
+    el = time.perf_counter() - t0
+    return dict(value=n * steps / el, seconds=el, cores=torch.get_num_threads(), n=n, contacts=contacts)
+
+
 def run_triaxial(args):
     """Cost of the gradient of the mean deviatoric stress over a 400-step
     window against the plain forward of the same window, and the gradient's
@@ -537,6 +572,13 @@ def run_triaxial(args):
         fd.append((objective(tp) - objective(tm)) / (2 * h))
     fd = np.array(fd) if fd else np.full(3, np.nan)
     contacts = info.contacts + info.geom_contacts
+    cpu = None
+    if not args.no_cpu_baseline:
+        s = oracle_gradient_sample()
+        cpu = {"value": s["value"], "unit": "particle-steps/s (forward + gradient)", "cores": s["cores"],
+               "kind": "oracle", "sample": (f"FP64 autograd gradient oracle, 1 step of a {s['n']}-sphere triaxial "
+                                            f"cell squeezed to contact ({s['contacts']} contacts), N_it 172, "
+                                            f"{s['seconds']:.1f} s")}
     bed.free_checkpoint(start)
     bed.close()
     return dict(adjoint_over_forward=t_adj / t_fwd, record_over_forward=t_rec / t_fwd,
@@ -546,6 +588,7 @@ def run_triaxial(args):
                 fd_rel_err=None if args.no_fd else (np.abs(grad - fd) / np.abs(fd).max()).tolist(),
                 particles=info.n,
                 contacts=contacts, peak_mem_gib=mem, prepare_s=t_prep, clocks=clk.summary(),
+                gradient_particle_steps_per_s=info.n * steps / (t_rec + t_adj), cpu_baseline=cpu,
                 sweep_layout=info.lanes, **prep)
 
 
@@ -614,7 +657,9 @@ def main():
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
                           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                           "config": {"workload": "fine bed shear: r 2.5 mm +-10%, depth 0.25 m, settled under gravity, "
-                                                 "grousered 0.3x0.3 m plate dragged at 0.05 m/s, dt 1e-5 s",
+                                                 "grousered 0.3x0.3 m plate under a 10 kPa normal load "
+                                                 "(vertical dynamics) dragged at 0.05 m/s, dt 1e-5 s",
+                                     "plate_force_N": r["plate_force_N"], "plate_z_m": r["plate_z"],
                                      "particles": r["n"], "contacts": r["contacts"], "n_it": r["n_it"],
                                      "contacts_at_start": r["contacts_at_start"], "footprint_m": r["footprint"],
                                      "sweep_layout": r["lanes"], "launch_params": "autotuner"},

@@ -499,6 +499,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     AL(B.glamW[0], 2 * GC); AL(B.glamW[1], 2 * GC);
     AL(B.geom, (size_t)std::max(P.ng, 1)); AL(B.gacc, 6 * (size_t)std::max(P.ng, 1));
     AL(B.grp, DEM_MAX_GROUPS); AL(B.gcnt, DEM_MAX_GROUPS); AL(B.gimp, 9 * DEM_MAX_GROUPS);
+    AL(B.gl_list, GC); AL(B.gl_count, 1);
     AL(B.key_a, N); AL(B.key_b, N); AL(B.val_a, N); AL(B.val_b, N);
     AL(B.hist, 256 * (size_t)nbr + 1);
     AL(B.t_pos, N); AL(B.t_vw, N); AL(B.t_id, N); AL(B.t_lvl, N);
@@ -558,6 +559,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     CK(cudaMemsetAsync(B.grp, 0, DEM_MAX_GROUPS * sizeof(GroupDev), s));
     CK(cudaMemsetAsync(B.gcnt, 0, DEM_MAX_GROUPS * sizeof(int), s));
     CK(cudaMemsetAsync(B.gimp, 0, 9 * DEM_MAX_GROUPS * sizeof(long long), s));
+    CK(cudaMemsetAsync(B.gl_count, 0, sizeof(int), s));
     CK(cudaStreamSynchronize(s));
 
     st = build_graphs(b);
@@ -611,6 +613,7 @@ static int body_pre(dem_bed* b, int p) {
     cudaMemsetAsync(B.in_fill, 0, (N + 1) * sizeof(int), s);
     cudaMemsetAsync(B.gacc, 0, 6 * std::max(P.ng, 1) * sizeof(long long), s);
     if (P.n_groups > 0) {
+        cudaMemsetAsync(B.gl_count, 0, sizeof(int), s);
         cudaMemsetAsync(B.gcnt, 0, DEM_MAX_GROUPS * sizeof(int), s);
         cudaMemsetAsync(B.gimp, 0, 9 * DEM_MAX_GROUPS * sizeof(long long), s);
     }

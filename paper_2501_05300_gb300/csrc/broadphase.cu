@@ -237,7 +237,11 @@ __global__ void __launch_bounds__(BP_T) k_contacts_build(SimParams P, DevBuf B, 
         if (gs + k >= gcap) { set_flag(B.err, DEM_FLAG_CAPACITY); break; }
         B.g_key[parity][gs + k] = gl[k];
         const int q = B.geom[gl[k]].grp;
-        if (q >= 0) atomicAdd(&B.gcnt[q], 1);   // split mass of a load-driven group
+        if (q >= 0) {   // a load-driven group: its split mass and its contact list
+            atomicAdd(&B.gcnt[q], 1);
+            const int slot = atomicAdd(B.gl_count, 1);
+            if (slot < gcap) B.gl_list[slot] = make_int2(gs + k, i);
+        }
     }
 }
 

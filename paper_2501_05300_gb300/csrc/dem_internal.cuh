@@ -158,6 +158,8 @@ struct DevBuf {
     int* gcnt;          // [DEM_MAX_GROUPS] contacts of each group this step
     long long* gimp;    // [3][DEM_MAX_GROUPS][3] fixed-point impulse on each group, per
                         //   iterate k (buffer k % 3): read at sweep k, written at k - 1
+    int2* gl_list;      // [max_geo] (contact, body) of every contact with a group's primitive
+    int* gl_count;      // [1] entries of gl_list this step
     // re-sort scratch
     unsigned* key_a; unsigned* key_b;
     int* val_a; int* val_b;
@@ -184,6 +186,8 @@ int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
 // nact: particles of the beds still sweeping at sweep `it` (a prefix of the slots)
 int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int nact, cudaStream_t s);
 int launch_integrate(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
+// contacts of load-driven groups at sweep it (before the sweep's body updates)
+int launch_group_contacts(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s);
 int launch_resort(const SimParams& P, const DevBuf& B, cudaStream_t s);
 int launch_radix_sort(unsigned* key_a, int* val_a, unsigned* key_b, int* val_b, int n, int* hist,
                       int* tmp, cudaStream_t s);

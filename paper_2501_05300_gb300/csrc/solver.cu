@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         r[2] = make_float4(la, G.mu_t, G.mu_r * ra, __int_as_float(g));
         r[3] = make_float4(vgp.x, vgp.y, vgp.z, i12);
         r[4] = make_float4(wg.x, wg.y, wg.z, i22);
-        r[5] = make_float4(lever.x, lever.y, lever.z, 0.f);
+        r[5] = make_float4(lever.x, lever.y, lever.z, __int_as_float(G.grp));
         B.g_delta[k] = delta;
         float4 l0 = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 l1 = make_float2(0.f, 0.f);
@@ -244,22 +244,39 @@ static __device__ __forceinline__ Upd contact_update(float4 r0, float4 r1, float
     return u;
 }
 
-// Update of sphere-geometry contact k at sweep it from the body's iterate
-// (vi, wi); a load-driven group's contact takes the group's iterate and adds
-// its impulse to the group's sum for iterate it + 1.
-static __device__ __forceinline__ Upd geom_update(const SimParams& P, const DevBuf& B, const float4* r, int k,
-                                                  int src, int it, float3 vi, float3 wi) {
-    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
-    const float4 l0 = B.glamA[src][k];
-    const float2 l1 = B.glamB[src][k];
-    const int q = B.geom[__float_as_int(r2.w)].grp;
-    if (q < 0) return contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4), P.eps_reg);
-    const float3 vgp = group_velocity(P, B, q, it) + cross(f3(r4), f3(r[5]));
+// A load-driven group's contact at sweep it: the group's iterate instead of
+// the primitive's prescribed velocity, and the contact's impulse added to the
+// group's sum for iterate it + 1 (k_group_contacts).
+static __device__ __forceinline__ Upd geom_update_group(const SimParams& P, const DevBuf& B, const float4* r,
+                                                        float4 l0, float2 l1, float3 vi, float3 wi, int q, int it) {
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+    const float3 vgp = group_velocity(P, B, q, it) + cross(f3(r4), f3(r5));
     const Upd u = contact_update<true>(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - vgp, wi, f3(r4), P.eps_reg,
                                        r3.w, r4.w);
     const float3 n = f3(r0);
     group_add(B, q, it + 1, (-1.0f) * (u.pn * n + u.pt1 * u.t1 + u.pt2 * u.t2));
     return u;
+}
+
+// Update of sphere-geometry contact k at sweep it from the body's iterate (vi, wi).
+// A group's contact was updated by k_group_contacts: its new impulse is read.
+static __device__ __forceinline__ Upd geom_update(const SimParams& P, const DevBuf& B, const float4* r, int k,
+                                                  int src, int it, float3 vi, float3 wi, bool& done) {
+    const float4 r0 = r[0];
+    done = __float_as_int(r[5].w) >= 0;
+    Upd u;
+    if (done) {
+        const int dst = src ^ 1;
+        const float4 a = B.glamA[dst][k];
+        const float2 b = B.glamB[dst][k];
+        tangent_basis(f3(r0), u.t1, u.t2);
+        u.pn = a.x; u.pt1 = a.y; u.pt2 = a.z; u.pr = make_float3(a.w, b.x, b.y);
+        return u;
+    }
+    const float4 r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+    const float4 l0 = B.glamA[src][k];
+    const float2 l1 = B.glamB[src][k];
+    return contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4), P.eps_reg);
 }
 
 static __device__ __forceinline__ void write_world(float4* W, size_t c, float3 n, const Upd& u) {
@@ -342,20 +359,21 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
             const float2 l1 = B.glamB[src][k];
             const float3 n = f3(r0);
             Upd u;
+            bool done = false;
             if (UPDATE) {
-                u = geom_update(P, B, r, k, src, it, vi, wi);
-                if (!last) {
+                u = geom_update(P, B, r, k, src, it, vi, wi, done);
+                if (!last && !done) {
                     B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
                     B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
                 }
             } else {
                 tangent_basis(n, u.t1, u.t2);
                 u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
-                const int q = B.geom[__float_as_int(r2.w)].grp;
+                const int q = __float_as_int(r[5].w);
                 if (q >= 0)   // the warm start's impulse on a load-driven group: iterate 0
                     group_add(B, q, 0, (-1.0f) * (u.pn * n + u.pt1 * u.t1 + u.pt2 * u.t2));
             }
-            if (last) write_world(B.glamW[p], k, n, u);
+            if (last && !done) write_world(B.glamW[p], k, n, u);
             add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
         }
     }
@@ -555,8 +573,10 @@ __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p
                 const float4* r = B.grec + 6 * (size_t)k;
                 const float4 r0 = r[0], r2 = r[2];
                 const float3 n = f3(r0);
-                const Upd u = geom_update(P, B, r, k, src, it, vi, wi);
-                if (last) {
+                bool done;
+                const Upd u = geom_update(P, B, r, k, src, it, vi, wi, done);
+                if (done) {
+                } else if (last) {
                     write_world(B.glamW[p], k, n, u);
                 } else {
                     B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
@@ -579,6 +599,34 @@ __global__ void __launch_bounds__(SV_T) k_body_pass(SimParams P, DevBuf B, int p
     out.v = make_float4(v.x, v.y, v.z, v0.w);
     out.w = make_float4(w.x, w.y, w.z, w0.w);
     B.vw[dst][i] = out;
+}
+
+// Contacts of load-driven groups at sweep it, one thread each: from the body's
+// iterate v^it and the group's, the new impulse (written where the sweep's
+// body update reads it) and its share of the group's sum for iterate it + 1.
+__global__ void __launch_bounds__(SV_T) k_group_contacts(SimParams P, DevBuf B, int p, int it) {
+    if (*B.err) return;
+    const int m = min(*B.gl_count, P.max_geo);
+    const int src = it & 1, dst = src ^ 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+        const int2 e = B.gl_list[t];
+        const int k = e.x, i = e.y;
+        const int nit = body_nit(P, B, i);
+        if (it >= nit) continue;
+        const float4* r = B.grec + 6 * (size_t)k;
+        const VW me = B.vw[src][i];
+        const Upd u = geom_update_group(P, B, r, B.glamA[src][k], B.glamB[src][k], f3(me.v), f3(me.w),
+                                        __float_as_int(r[5].w), it);
+        B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+        B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
+        if (it == nit - 1) write_world(B.glamW[p], k, f3(r[0]), u);
+    }
+}
+
+int launch_group_contacts(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s) {
+    if (P.n_groups == 0) return 0;
+    k_group_contacts<<<64, SV_T, 0, s>>>(P, B, parity, it);
+    return 1;
 }
 
 template <typename K>
@@ -617,7 +665,7 @@ static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int it
 
 static void sweep_dispatch(const SimParams& P, const DevBuf& B, int parity, int it, int nact, bool update,
                            cudaStream_t s) {
-    switch (P.lanes > 0 && P.lanes <= 8 ? P.lanes : 2) {
+    switch (P.lanes > 0 ? P.lanes : 2) {
         case 1: sweep_launch<1>(P, B, parity, it, nact, update, s); break;
         case 2: sweep_launch<2>(P, B, parity, it, nact, update, s); break;
         case 8: sweep_launch<8>(P, B, parity, it, nact, update, s); break;
@@ -633,16 +681,18 @@ int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
 }
 
 int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int nact, cudaStream_t s) {
-    if (P.lanes > 0 && P.lanes <= 8) {   // single-kernel sweep, T threads per body
+    if (P.lanes > 0) {   // single-kernel sweep, T threads per body
+        const int kg = launch_group_contacts(P, B, parity, it, s);
         sweep_dispatch(P, B, parity, it, nact, true, s);
-        return 1;
+        return 1 + kg;
     }
     // two-pass sweep: contacts (grid-stride) then bodies
     const int cblocks = std::max(1, std::min(nblk(nact * 8, SV_T), 16 * sm_count()));
     const int bblocks = nblk(nact * BT, SV_T);
     launch_pdl(k_contact_pass, cblocks, s, P, B, parity, it, nact);
+    const int kg = launch_group_contacts(P, B, parity, it, s);
     launch_pdl(k_body_pass, bblocks, s, P, B, parity, it, nact);
-    return 2;
+    return 2 + kg;
 }
 
 int launch_integrate(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {

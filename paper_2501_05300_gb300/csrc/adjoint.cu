@@ -42,6 +42,25 @@
 
 static inline int nblk(long long n, int t) { return n > 0 ? (int)((n + t - 1) / t) : 1; }
 
+// Programmatic dependent launch: a kernel may start while the previous one
+// drains; it waits (griddepcontrol.wait) before touching what that one wrote.
+static __device__ __forceinline__ void adj_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+static __device__ __forceinline__ void adj_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl_adj(void (*kernel)(KArgs...), int blocks, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(AD_T);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---------------------------------------------------------------------------
 // host-side records
 // ---------------------------------------------------------------------------
@@ -115,6 +134,9 @@ struct AdjointState {
     std::vector<TapeStep> tape;     // one per step of the segment being reversed
     long long* fhist = nullptr;     // [nsteps * 6 ng] fixed-point geometry impulses
     size_t fhist_n = 0;
+    int* cnt_dev = nullptr;         // [2 nsteps] contacts of each recorded step (sphere, geometry)
+    size_t cnt_n = 0;
+    std::vector<int> counts;        // host copy of cnt_dev
     float* wts = nullptr;           // [nsteps * ng * 3] dJ/dF
     size_t wts_n = 0;
     // adjoint of the state between steps (current slot order), ping-pong
@@ -340,6 +362,8 @@ __global__ void __launch_bounds__(AD_T) k_tape_iter(int n, int nc, int ngc, cons
                                                     const float2* __restrict__ lB, const float4* __restrict__ gA,
                                                     const float2* __restrict__ gB, const VW* __restrict__ v,
                                                     float4* oA, float2* oB, float4* ogA, float2* ogB, VW* ov) {
+    adj_pdl_wait();
+    adj_pdl_trigger();
     const long long total = (long long)nc + ngc + n;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
@@ -414,6 +438,8 @@ __global__ void __launch_bounds__(AD_T) k_adj_init(SimParams P, TapeStep T, AdjB
 
 // reverse of sweep k, sphere-sphere contacts: one thread per contact
 __global__ void __launch_bounds__(AD_T) k_adj_contacts(SimParams P, TapeStep T, AdjBufs Q, int k) {
+    adj_pdl_wait();
+    adj_pdl_trigger();
     const int src = (k + 1) & 1;
     const VW* __restrict__ vk = T.v + (size_t)k * P.n;
     const VW* __restrict__ gb = Q.vb[src];
@@ -450,6 +476,8 @@ __global__ void __launch_bounds__(AD_T) k_adj_contacts(SimParams P, TapeStep T, 
 // reverse of sweep k, bodies: v-bar^k = sum of the shares (incidence order)
 // plus the body's primitive contacts, reversed here
 __global__ void __launch_bounds__(AD_T) k_adj_bodies(SimParams P, TapeStep T, AdjBufs Q, int k) {
+    adj_pdl_wait();
+    adj_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const int src = (k + 1) & 1, dst = k & 1;
@@ -794,7 +822,9 @@ static dem_status restore_checkpoint(dem_bed* b, const Checkpoint& K) {
 // ---------------------------------------------------------------------------
 // host: one step recomputed with its tape
 // ---------------------------------------------------------------------------
-static dem_status tape_step(dem_bed* b, TapeStep& T) {
+// counts: this step's and the previous step's contacts (known from dem_record,
+// so that the recompute needs no synchronisation)
+static dem_status tape_step(dem_bed* b, TapeStep& T, int nc, int ngc, int ncp, int ngcp) {
     const SimParams& P = b->P;
     const DevBuf& B = b->B;
     cudaStream_t s = b->stream;
@@ -803,11 +833,9 @@ static dem_status tape_step(dem_bed* b, TapeStep& T) {
     const int p = (int)(b->steps & 1), q = p ^ 1;
     if (resort) DEM_CK(cudaGraphLaunch(b->g_resort, s));
     DEM_CK(cudaGraphLaunch(b->g[p][0], s));   // contacts, rows, warm start, v^0
-    int nc = 0, ngc = 0, ncp = 0, ngcp = 0;
-    dem_status st = read_counts(b, p, &nc, &ngc);
-    if (st == DEM_OK) st = read_counts(b, q, &ncp, &ngcp);
-    if (st != DEM_OK) return st;
+    (void)q;
     T.nc = nc; T.ngc = ngc; T.nc_prev = ncp; T.ngc_prev = ngcp;
+    dem_status st;
     T.resorted = resort ? 1 : 0;
     T.step = b->steps;
     const size_t it = std::max(nit, 1);
@@ -837,9 +865,10 @@ static dem_status tape_step(dem_bed* b, TapeStep& T) {
     k_tape_bodies<<<nblk(n, AD_T), AD_T, 0, s>>>(P, B, p, T);
     const int gi = std::min(nblk((long long)nc + ngc + n, AD_T), 8 * 152);
     auto iter = [&](int k, int from) {
-        k_tape_iter<<<gi, AD_T, 0, s>>>(n, nc, ngc, B.lamA[from], B.lamB[from], B.glamA[from], B.glamB[from],
-                                        B.vw[from], T.lamA + (size_t)k * nc, T.lamB + (size_t)k * nc,
-                                        T.glamA + (size_t)k * ngc, T.glamB + (size_t)k * ngc, T.v + (size_t)k * n);
+        launch_pdl_adj(k_tape_iter, gi, s, n, nc, ngc, (const float4*)B.lamA[from], (const float2*)B.lamB[from],
+                       (const float4*)B.glamA[from], (const float2*)B.glamB[from], (const VW*)B.vw[from],
+                       T.lamA + (size_t)k * nc, T.lamB + (size_t)k * nc, T.glamA + (size_t)k * ngc,
+                       T.glamB + (size_t)k * ngc, T.v + (size_t)k * n);
     };
     iter(0, 0);   // lambda^0, v^0 (with no sweeps, also the final iterate)
     for (int k = 0; k < nit; ++k) {
@@ -874,8 +903,8 @@ static dem_status reverse_step(dem_bed* b, const TapeStep& T, int cur, int widx)
     k_adj_init<<<gi, AD_T, 0, s>>>(P, T, Q, nit & 1);
     const int cb = std::max(1, std::min(nblk(T.nc, AD_T), 16 * 152));
     for (int k = nit - 1; k >= 0; --k) {
-        k_adj_contacts<<<cb, AD_T, 0, s>>>(P, T, Q, k);
-        k_adj_bodies<<<nblk(n, AD_T), AD_T, 0, s>>>(P, T, Q, k);
+        DEM_CK(launch_pdl_adj(k_adj_contacts, cb, s, P, T, Q, k));
+        DEM_CK(launch_pdl_adj(k_adj_bodies, nblk(n, AD_T), s, P, T, Q, k));
     }
     // the previous step's final impulses: only those continued here get an adjoint
     if (T.nc_prev > 0) DEM_CK(cudaMemsetAsync(Q.lw_out, 0, 2 * (size_t)T.nc_prev * sizeof(float4), s));
@@ -998,13 +1027,28 @@ extern "C" dem_status dem_record(dem_bed* b, int32_t nsteps, int32_t ckpt_every,
         if ((st = dem_dalloc(b, (void**)&S->fhist, fn * sizeof(long long))) != DEM_OK) return st;
         S->fhist_n = fn;
     }
+    if ((size_t)(2 * nsteps) > S->cnt_n) {
+        if (S->cnt_dev) dem_dfree(b, S->cnt_dev);
+        S->cnt_dev = nullptr;
+        S->cnt_n = 0;
+        if ((st = dem_dalloc(b, (void**)&S->cnt_dev, 2 * (size_t)nsteps * sizeof(int))) != DEM_OK) return st;
+        S->cnt_n = 2 * (size_t)nsteps;
+    }
     for (int t = 0; t < nsteps; ++t) {
         if (t % ckpt_every == 0 && (st = save_checkpoint(b, S->ck[t / ckpt_every])) != DEM_OK) return st;
+        const int p = (int)(b->steps & 1);
         if ((st = dem_launch_step(b)) != DEM_OK) return st;
         DEM_CK(cudaMemcpyAsync(S->fhist + (size_t)t * 6 * ng, b->B.gacc, 6 * ng * sizeof(long long),
                                cudaMemcpyDeviceToDevice, b->stream));
+        DEM_CK(cudaMemcpyAsync(S->cnt_dev + 2 * t, b->B.own_start[p] + b->P.n, sizeof(int),
+                               cudaMemcpyDeviceToDevice, b->stream));
+        DEM_CK(cudaMemcpyAsync(S->cnt_dev + 2 * t + 1, b->B.geo_start[p] + b->P.n, sizeof(int),
+                               cudaMemcpyDeviceToDevice, b->stream));
     }
     if ((st = save_checkpoint(b, S->end)) != DEM_OK) return st;
+    S->counts.assign(2 * (size_t)nsteps, 0);
+    DEM_CK(cudaMemcpyAsync(S->counts.data(), S->cnt_dev, 2 * (size_t)nsteps * sizeof(int), cudaMemcpyDeviceToHost,
+                           b->stream));
     if ((st = dem_check_fault(b)) != DEM_OK) return st;
     if (forces) {
         std::vector<long long> h(fn);
@@ -1077,7 +1121,12 @@ extern "C" dem_status dem_step_adjoint(dem_bed* b, const double* dJ_dF, double g
     for (int seg = nseg - 1; seg >= 0 && st == DEM_OK; --seg) {
         const int first = seg * S->every, len = std::min(S->every, S->nsteps - first);
         if ((st = restore_checkpoint(b, S->ck[seg])) != DEM_OK) break;
-        for (int j = 0; j < len && st == DEM_OK; ++j) st = tape_step(b, S->tape[j]);
+        for (int j = 0; j < len && st == DEM_OK; ++j) {
+            const int t = first + j;
+            const int ncp = t > 0 ? S->counts[2 * (t - 1)] : S->ck[0].nc_prev;
+            const int ngcp = t > 0 ? S->counts[2 * (t - 1) + 1] : S->ck[0].ngc_prev;
+            st = tape_step(b, S->tape[j], S->counts[2 * t], S->counts[2 * t + 1], ncp, ngcp);
+        }
         for (int j = len - 1; j >= 0 && st == DEM_OK; --j) {
             st = reverse_step(b, S->tape[j], cur, first + j);
             cur ^= 1;

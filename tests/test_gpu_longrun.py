@@ -76,6 +76,7 @@ def test_pressure_sinkage_curve(settled):
     scale = np.abs(fo).max()
     assert scale > 0.5            # the plate is pushing into the bed
     ne = np.mean(np.abs(fg - fo)) / scale
+    print(f"pressure-sinkage: normalised force error {ne:.5f}, peak force {scale:.3f} N")
     assert ne < 0.02, ne
 
 
@@ -112,5 +113,7 @@ def test_shear_displacement_curve(settled):
     assert so[0, 1] - so[-1, 1] > 0                       # the loaded plate sinks
     ne_t = np.mean(np.abs(sg[:, 0] - so[:, 0])) / F_N
     ne_z = np.mean(np.abs(sg[:, 1] - so[:, 1])) / h_grouser
+    print(f"shear-displacement: normalised traction error {ne_t:.5f}, sinkage error {ne_z:.5f}, "
+          f"peak traction {np.abs(so[:, 0]).max():.3f} N, sinkage {so[0, 1] - so[-1, 1]:.2e} m")
     assert ne_t < 0.02, ne_t
     assert ne_z < 0.02, ne_z

@@ -14,6 +14,10 @@ Parity status per function (what pins it is in tests/test_oracle_*.py):
   Jacobi sweep                pinned: converges to the MCP solution found by an
                               independent projected Gauss-Seidel on tiny cases
   step-size / iteration rules pinned: Table 3 of the paper
+  coloured PGS (solver = 1)   pinned: reaches the Jacobi solution where the
+                              problem has one (frictionless), converges faster,
+                              meets the resting-column static limit; colour
+                              count within the greedy-colouring bounds
   load-driven plate groups    pinned: free fall under load equals the discrete
                               sum of the step; a loaded plate on a sphere on a
                               floor reaches the Hertz static overlaps; particle

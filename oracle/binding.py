@@ -38,7 +38,7 @@ class _Params(C.Structure):
                 ("mu_t", C.c_double), ("mu_r", C.c_double), ("e_H", C.c_double),
                 ("damp_steps", C.c_double), ("dt", C.c_double), ("n_it", C.c_int32),
                 ("gravity", C.c_double * 3), ("kn_scale", C.c_double),
-                ("eps_reg", C.c_double), ("delta_floor", C.c_double)]
+                ("eps_reg", C.c_double), ("delta_floor", C.c_double), ("solver", C.c_int32)]
 
 
 class _Geom(C.Structure):
@@ -63,6 +63,7 @@ class OracleParams:
     kn_scale: float = 1.0
     eps_reg: float = 1e-6
     delta_floor: float = 1e-8
+    solver: int = 0              # 0 Jacobi with mass splitting, 1 coloured projected Gauss-Seidel
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -70,6 +71,7 @@ class OracleParams:
                   "eps_reg", "delta_floor"):
             setattr(p, k, float(getattr(self, k)))
         p.n_it = int(self.n_it)
+        p.solver = int(self.solver)
         p.gravity = (C.c_double * 3)(*[float(v) for v in self.gravity])
         return p
 
@@ -132,6 +134,9 @@ def load():
         lib.orc_get_contacts.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp]
         lib.orc_set_warmstart.argtypes = [vp, C.c_int64, i32, i32, d]
         lib.orc_threads.restype = C.c_int
+        lib.orc_colours.restype = C.c_int32
+        lib.orc_colours.argtypes = [vp]
+        lib.orc_step.restype = C.c_int
         lib.orc_set_load.restype = C.c_int
         lib.orc_set_load.argtypes = [vp, C.c_int32, i32, C.c_double, d, C.c_int32]
         _lib = lib
@@ -194,7 +199,12 @@ class Oracle:
             self.h = None
 
     def step(self, nsteps=1):
-        self.lib.orc_step(self.h, int(nsteps))
+        if self.lib.orc_step(self.h, int(nsteps)) != 0:
+            raise ValueError("the PGS solver does not take load-driven groups")
+
+    def colours(self):
+        """Colours of the last PGS step (0 for Jacobi)."""
+        return int(self.lib.orc_colours(self.h))
 
     def state(self):
         x = np.zeros((self.n, 3)); v = np.zeros((self.n, 3)); w = np.zeros((self.n, 3))

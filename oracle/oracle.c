@@ -262,6 +262,7 @@ struct orc_sim {
     ws_entry* ws;
     int64_t nws;
     double* gforce; /* 6 per geometry */
+    int32_t ncol;     /* colours of the last PGS step */
     /* load-driven rigid groups of primitives (orc_set_load) */
     int32_t ngrp;
     int32_t* gbody;   /* per primitive: its group, or -1 (kinematic) */
@@ -465,6 +466,63 @@ static void add_GT(double G[6][6], const double* lam, double* acc) {
 /* ------------------------------------------------------------------------- */
 /* one SPOOK step                                                             */
 /* ------------------------------------------------------------------------- */
+/* One projected update of contact c (Eqs. 5-7) from the body velocities
+ * (vv, ww) and, for a load-driven group's primitive, the group velocity vg. */
+static void project_contact(const contact* c, const double* vv, const double* ww, const double* vg,
+                            double* out) {
+    double wres[6];
+    for (int row = 0; row < 6; ++row) {
+        double gv = dot3(c->Ga[row], &vv[3 * c->a]) + dot3(&c->Ga[row][3], &ww[3 * c->a]);
+        if (c->b >= 0) gv += dot3(c->Gb[row], &vv[3 * c->b]) + dot3(&c->Gb[row][3], &ww[3 * c->b]);
+        else if (vg) gv += dot3(c->Gb[row], vg) + c->known_ang[row];
+        else gv += c->known[row];
+        wres[row] = gv + c->sig[row] * c->lam[row] - c->rhs[row];
+    }
+    /* normal: 0 <= lambda_n (Eq. 5) */
+    double ln = c->lam[0] - c->Dn_inv * wres[0];
+    if (ln < 0.0) ln = 0.0;
+    /* tangential: Coulomb disc |lambda_t| <= mu_t lambda_n (Eq. 6) */
+    double lt[2];
+    for (int i = 0; i < 2; ++i) lt[i] = c->lam[1 + i] - (c->Dt_inv[i][0] * wres[1] + c->Dt_inv[i][1] * wres[2]);
+    double ltn = sqrt(lt[0] * lt[0] + lt[1] * lt[1]);
+    double bt = c->mu_t * ln;
+    if (ltn > bt) { lt[0] *= bt / ltn; lt[1] *= bt / ltn; }
+    /* rolling: ball |lambda_r| <= mu_r r lambda_n (Eq. 7) */
+    double lr[3];
+    for (int i = 0; i < 3; ++i)
+        lr[i] = c->lam[3 + i] - (c->Dr_inv[i][0] * wres[3] + c->Dr_inv[i][1] * wres[4] + c->Dr_inv[i][2] * wres[5]);
+    double lrn = sqrt(lr[0] * lr[0] + lr[1] * lr[1] + lr[2] * lr[2]);
+    double br = c->mu_r_reff * ln;
+    if (lrn > br) { for (int i = 0; i < 3; ++i) lr[i] *= br / lrn; }
+    out[0] = ln;
+    out[1] = lt[0]; out[2] = lt[1];
+    out[3] = lr[0]; out[4] = lr[1]; out[5] = lr[2];
+}
+
+/* SplitMix64 finaliser (Steele, Lea and Flood 2014; Vigna): the priority of a
+ * contact is the mix of its key (stable id of a, stable id of b or -(g+1)). */
+static uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+static uint64_t contact_key(const contact* c) { return ((uint64_t)(uint32_t)c->ka << 32) | (uint32_t)c->kb; }
+
+/* higher priority first; equal mixes (not expected) by key */
+static int before(const contact* x, const contact* y) {
+    const uint64_t kx = contact_key(x), ky = contact_key(y);
+    const uint64_t px = mix64(kx), py = mix64(ky);
+    return px != py ? px > py : kx < ky;
+}
+
+static const contact* g_sort_base;
+static int cmp_priority(const void* pa, const void* pb) {
+    const contact* x = &g_sort_base[*(const int64_t*)pa];
+    const contact* y = &g_sort_base[*(const int64_t*)pb];
+    return before(x, y) ? -1 : (before(y, x) ? 1 : 0);
+}
+
 static void step_once(orc_sim* s) {
     const orc_params* P = &s->p;
     const double h = P->dt;
@@ -577,9 +635,13 @@ static void step_once(orc_sim* s) {
 
         /* block diagonal of G Msplit^-1 G^T + Sigma */
         double D[6][6];
-        const double ima = cnt[a] * s->inv_m[a], iIa = cnt[a] * s->inv_I[a];
-        const double imb = c->b >= 0 ? cnt[c->b] * s->inv_m[c->b] : 0.0;
-        const double iIb = c->b >= 0 ? cnt[c->b] * s->inv_I[c->b] : 0.0;
+        /* Jacobi splits each body's mass over its contacts (m / n_b); Gauss-Seidel
+         * updates bodies between contacts and uses the masses themselves */
+        const double spa = P->solver == ORC_PGS ? 1.0 : cnt[a];
+        const double spb = c->b >= 0 ? (P->solver == ORC_PGS ? 1.0 : cnt[c->b]) : 0.0;
+        const double ima = spa * s->inv_m[a], iIa = spa * s->inv_I[a];
+        const double imb = c->b >= 0 ? spb * s->inv_m[c->b] : 0.0;
+        const double iIb = c->b >= 0 ? spb * s->inv_I[c->b] : 0.0;
         /* inverse (split) mass of side b per axis: a particle's, a load-driven
          * group's along its dynamic axes, zero for kinematic geometry */
         double imb3[3] = {imb, imb, imb};
@@ -677,43 +739,77 @@ static void step_once(orc_sim* s) {
     BODY_UPDATE();
     GROUP_UPDATE();
 
-    /* 3. N_it projected Jacobi sweeps */
-    for (int32_t it = 0; it < P->n_it; ++it) {
-#pragma omp parallel for schedule(static)
-        for (int64_t k = 0; k < s->nc; ++k) {
-            contact* c = &s->c[k];
-            double wres[6];
-            for (int row = 0; row < 6; ++row) {
-                double gv = dot3(c->Ga[row], &vv[3 * c->a]) + dot3(&c->Ga[row][3], &ww[3 * c->a]);
-                if (c->b >= 0) gv += dot3(c->Gb[row], &vv[3 * c->b]) + dot3(&c->Gb[row][3], &ww[3 * c->b]);
-                else if (c->grp >= 0) gv += dot3(c->Gb[row], vg[c->grp]) + c->known_ang[row];
-                else gv += c->known[row];
-                wres[row] = gv + c->sig[row] * c->lam[row] - c->rhs[row];
+    /* 3. N_it projected sweeps */
+    s->ncol = 0;
+    if (P->solver == ORC_PGS) {
+        /* Colours: contacts that share a body never share a colour.  Greedy in
+         * priority order, each contact taking the smallest colour that none of
+         * its already coloured neighbours has. */
+        int32_t* col = (int32_t*)malloc((size_t)(s->nc ? s->nc : 1) * sizeof(int32_t));
+        int64_t* order = (int64_t*)malloc((size_t)(s->nc ? s->nc : 1) * sizeof(int64_t));
+        for (int64_t k = 0; k < s->nc; ++k) { col[k] = -1; order[k] = k; }
+        g_sort_base = s->c;
+        qsort(order, (size_t)s->nc, sizeof(int64_t), cmp_priority);
+        int32_t ncol = 0;
+        for (int64_t q = 0; q < s->nc; ++q) {
+            const int64_t k = order[q];
+            const contact* c = &s->c[k];
+            unsigned char used[256];
+            memset(used, 0, sizeof used);
+            const int bodies[2] = {c->a, c->b};
+            for (int e2 = 0; e2 < 2; ++e2) {
+                const int body = bodies[e2];
+                if (body < 0) continue;
+                for (int64_t e = start[body]; e < start[body + 1]; ++e) {
+                    const int64_t m = inc[e] / 2;
+                    if (m != k && col[m] >= 0 && col[m] < 256) used[col[m]] = 1;
+                }
             }
-            /* normal: 0 <= lambda_n (Eq. 5) */
-            double ln = c->lam[0] - c->Dn_inv * wres[0];
-            if (ln < 0.0) ln = 0.0;
-            /* tangential: Coulomb disc |lambda_t| <= mu_t lambda_n (Eq. 6) */
-            double lt[2];
-            for (int i = 0; i < 2; ++i)
-                lt[i] = c->lam[1 + i] - (c->Dt_inv[i][0] * wres[1] + c->Dt_inv[i][1] * wres[2]);
-            double ltn = sqrt(lt[0] * lt[0] + lt[1] * lt[1]);
-            double bt = c->mu_t * ln;
-            if (ltn > bt) { lt[0] *= bt / ltn; lt[1] *= bt / ltn; }
-            /* rolling: ball |lambda_r| <= mu_r r lambda_n (Eq. 7) */
-            double lr[3];
-            for (int i = 0; i < 3; ++i)
-                lr[i] = c->lam[3 + i] - (c->Dr_inv[i][0] * wres[3] + c->Dr_inv[i][1] * wres[4] + c->Dr_inv[i][2] * wres[5]);
-            double lrn = sqrt(lr[0] * lr[0] + lr[1] * lr[1] + lr[2] * lr[2]);
-            double br = c->mu_r_reff * ln;
-            if (lrn > br) { for (int i = 0; i < 3; ++i) lr[i] *= br / lrn; }
-            c->lam_new[0] = ln;
-            c->lam_new[1] = lt[0]; c->lam_new[2] = lt[1];
-            c->lam_new[3] = lr[0]; c->lam_new[4] = lr[1]; c->lam_new[5] = lr[2];
+            int32_t cc = 0;
+            while (cc < 255 && used[cc]) ++cc;
+            col[k] = cc;
+            if (cc + 1 > ncol) ncol = cc + 1;
         }
-        for (int64_t k = 0; k < s->nc; ++k) memcpy(s->c[k].lam, s->c[k].lam_new, 6 * sizeof(double));
-        BODY_UPDATE();
-        GROUP_UPDATE();
+        s->ncol = ncol;
+        /* sweeps: colour by colour, each contact's impulse change applied to
+         * its bodies at once (no two contacts of a colour share a body) */
+        for (int32_t it = 0; it < P->n_it; ++it)
+            for (int32_t cc = 0; cc < ncol; ++cc)
+                for (int64_t k = 0; k < s->nc; ++k) {
+                    if (col[k] != cc) continue;
+                    contact* c = &s->c[k];
+                    double nl[6], d[6], acc[6];
+                    project_contact(c, vv, ww, NULL, nl);
+                    for (int q = 0; q < 6; ++q) d[q] = nl[q] - c->lam[q];
+                    memset(acc, 0, sizeof acc);
+                    add_GT(c->Ga, d, acc);
+                    for (int q = 0; q < 3; ++q) {
+                        vv[3 * c->a + q] += s->inv_m[c->a] * acc[q];
+                        ww[3 * c->a + q] += s->inv_I[c->a] * acc[3 + q];
+                    }
+                    if (c->b >= 0) {
+                        memset(acc, 0, sizeof acc);
+                        add_GT(c->Gb, d, acc);
+                        for (int q = 0; q < 3; ++q) {
+                            vv[3 * c->b + q] += s->inv_m[c->b] * acc[q];
+                            ww[3 * c->b + q] += s->inv_I[c->b] * acc[3 + q];
+                        }
+                    }
+                    memcpy(c->lam, nl, sizeof nl);
+                }
+        free(col);
+        free(order);
+    } else {
+        for (int32_t it = 0; it < P->n_it; ++it) {
+#pragma omp parallel for schedule(static)
+            for (int64_t k = 0; k < s->nc; ++k) {
+                contact* c = &s->c[k];
+                project_contact(c, vv, ww, c->grp >= 0 ? vg[c->grp] : NULL, c->lam_new);
+            }
+            for (int64_t k = 0; k < s->nc; ++k) memcpy(s->c[k].lam, s->c[k].lam_new, 6 * sizeof(double));
+            BODY_UPDATE();
+            GROUP_UPDATE();
+        }
     }
     #undef BODY_UPDATE
     #undef GROUP_UPDATE
@@ -776,7 +872,10 @@ static void step_once(orc_sim* s) {
     free(cnt); free(start); free(inc); free(fill); free(vs); free(vv); free(ww);
 }
 
+int32_t orc_colours(const orc_sim* s) { return s->ncol; }
+
 int orc_step(orc_sim* s, int32_t nsteps) {
+    if (s->p.solver == ORC_PGS && s->ngrp > 0) return -1;
     for (int32_t k = 0; k < nsteps; ++k) step_once(s);
     return 0;
 }

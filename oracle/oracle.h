@@ -47,7 +47,11 @@ typedef struct orc_params {
     double kn_scale;     /* multiplies k_n (1 = paper) */
     double eps_reg;      /* tangential/rolling compliance relative to the normal one */
     double delta_floor;  /* floor on the overlap inside the Hertz Jacobian factor [m] */
+    int32_t solver;      /* ORC_JACOBI (Jacobi with mass splitting) or ORC_PGS (coloured
+                            projected Gauss-Seidel, the paper's PGS ordered by contact colours) */
 } orc_params;
+
+enum { ORC_JACOBI = 0, ORC_PGS = 1 };
 
 typedef struct orc_geom {
     int32_t type;        /* ORC_PLANE, ORC_BOX, ORC_CYLINDER */
@@ -86,7 +90,10 @@ void orc_destroy(orc_sim* s);
  * for bad arguments or a primitive already in a group. */
 int orc_set_load(orc_sim* s, int32_t count, const int32_t* geoms, double mass, const double force[3],
                  int32_t dof);
+/* Returns 0, or -1 (nothing done) for the PGS solver with load-driven groups. */
 int orc_step(orc_sim* s, int32_t nsteps);
+/* Colours used by the last step's PGS sweeps (0 for Jacobi). */
+int32_t orc_colours(const orc_sim* s);
 void orc_get_state(const orc_sim* s, double* x, double* v, double* w);
 void orc_set_state(orc_sim* s, const double* x, const double* v, const double* w);
 void orc_set_geom_velocity(orc_sim* s, int32_t g, const double v[3], const double w[3]);

@@ -99,6 +99,12 @@ typedef struct dem_bed_desc {
     dem_alloc_fn alloc;         /* optional allocator (see above) */
     dem_free_fn free_fn;
     void* alloc_ctx;
+    int32_t solver;             /* 0 = projected Jacobi with mass splitting (default);
+                                   1 = coloured projected Gauss-Seidel (the paper's PGS, Sec. 2.2):
+                                   contacts coloured so that no two of a colour share a body, swept
+                                   colour by colour with the bodies updated in between, unsplit
+                                   masses.  PGS runs outside CUDA graphs (a study mode), needs the
+                                   same n_it in every bed, no load-driven groups, no adjoint. */
 } dem_bed_desc;
 
 typedef struct dem_bed dem_bed;   /* opaque, library-owned */
@@ -116,6 +122,8 @@ typedef struct dem_info {
     int32_t n_beds;             /* beds advanced together (dem_create_batch) */
     int32_t lanes;              /* current sweep layout (see dem_bed_desc.lanes) */
     int32_t resort_every;       /* current Morton re-sort period */
+    int32_t solver;             /* current solver (see dem_bed_desc.solver) */
+    int32_t colours;            /* colours of the last PGS step, 0 for Jacobi */
 } dem_info;
 
 /* Create a bed from particles, materials and geometry.

@@ -923,6 +923,7 @@ static dem_status reverse_step(dem_bed* b, const TapeStep& T, int cur, int widx)
 static dem_status check_supported(dem_bed* b) {
     const SimParams& P = b->P;
     if (!P.nit_uniform) return dem_fail(DEM_ERR_ARG, "the adjoint needs the same n_it in every bed");
+    if (P.solver) return dem_fail(DEM_ERR_ARG, "the adjoint reverses the Jacobi solver only");
     std::vector<GeomDev> hg(std::max(P.ng, 1));
     if (P.ng > 0) {
         // ordered after pending velocity changes on the bed's stream

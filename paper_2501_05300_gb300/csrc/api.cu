@@ -440,6 +440,16 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     P.max_contacts = (int)cap;
     P.max_geo = 2 * n + 1024;
     P.lanes = d->lanes;   // 0: two-pass sweep; 1, 2, 4, 8: one kernel, that many threads per body
+    P.solver = d->solver;
+    if (P.solver != 0 && P.solver != 1) {
+        release(b);
+        return fail(DEM_ERR_ARG, "solver = %d is not 0 (Jacobi) or 1 (coloured Gauss-Seidel)", d->solver);
+    }
+    for (int k = 1; k < nbeds && P.solver; ++k)
+        if (descs[k].n_it != descs[0].n_it) {
+            release(b);
+            return fail(DEM_ERR_ARG, "the Gauss-Seidel solver needs the same n_it in every bed");
+        }
     if (P.lanes != 0 && P.lanes != 1 && P.lanes != 2 && P.lanes != 4 && P.lanes != 8) {
         release(b);
         return fail(DEM_ERR_ARG, "lanes = %d is not 0, 1, 2, 4 or 8", d->lanes);
@@ -720,12 +730,74 @@ static dem_status check_fault(dem_bed* b) {
 
 dem_status dem_check_fault(dem_bed* b) { return check_fault(b); }
 
+// One coloured projected Gauss-Seidel solve (solver 1) between the pre and post
+// graphs: colour the step's contacts, then N_it sweeps of one kernel per colour.
+// The colour count is only known on the device, so this runs outside graphs.
+static dem_status pgs_solve(dem_bed* b, int p) {
+    const SimParams& P = b->P;
+    const DevBuf& B = b->B;
+    cudaStream_t s = b->stream;
+    int counts[2] = {0, 0};
+    CK(cudaMemcpyAsync(&counts[0], B.own_start[p] + P.n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&counts[1], B.geo_start[p] + P.n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int nc = std::min(counts[0], P.max_contacts), ngc = std::min(counts[1], P.max_geo);
+    const int total = nc + ngc;
+    PgsBuf& S = b->pgs;
+    if (!S.col) {   // at capacity, once
+        const size_t cap = (size_t)P.max_contacts + P.max_geo;
+        dem_status st = DEM_OK;
+        auto al = [&](void** q, size_t bytes) { if (st == DEM_OK) st = dalloc(b, q, bytes); };
+        al((void**)&S.col, cap * sizeof(int));
+        al((void**)&S.prio, cap * sizeof(unsigned long long));
+        al((void**)&S.key, cap * sizeof(unsigned long long));
+        al((void**)&S.gbody, (size_t)P.max_geo * sizeof(int));
+        al((void**)&S.list, cap * sizeof(int));
+        al((void**)&S.remaining, sizeof(int));
+        al((void**)&S.ncol, sizeof(int));
+        al((void**)&S.colcnt, PGS_MAX_COLOURS * sizeof(int));
+        al((void**)&S.colstart, PGS_MAX_COLOURS * sizeof(int));
+        al((void**)&S.colfill, PGS_MAX_COLOURS * sizeof(int));
+        if (st != DEM_OK) return st;
+        b->pgs_cap = (int64_t)cap;
+    }
+    launch_pgs_prepare(P, B, S, p, nc, ngc, s);
+    // colouring rounds until every contact has a colour (bounded)
+    int remaining = total, rounds = 0;
+    while (remaining > 0) {
+        if (rounds >= 4096) return fail(DEM_ERR_STATE, "contact colouring did not finish");
+        for (int k = 0; k < 8; ++k) launch_pgs_round(P, B, S, p, nc, ngc, s);
+        rounds += 8;
+        CK(cudaMemcpyAsync(&remaining, S.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    int ncol = 0;
+    launch_pgs_bucket(S, total, false, s);
+    std::vector<int> cnt(PGS_MAX_COLOURS, 0), start(PGS_MAX_COLOURS, 0);
+    CK(cudaMemcpyAsync(&ncol, S.ncol, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(cnt.data(), S.colcnt, PGS_MAX_COLOURS * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int c = 1; c < PGS_MAX_COLOURS; ++c) start[c] = start[c - 1] + cnt[c - 1];
+    CK(cudaMemcpyAsync(S.colstart, start.data(), PGS_MAX_COLOURS * sizeof(int), cudaMemcpyHostToDevice, s));
+    launch_pgs_bucket(S, total, true, s);
+    for (int it = 0; it < P.n_it; ++it)
+        for (int c = 0; c < ncol; ++c)
+            if (cnt[c] > 0) launch_pgs_colour(P, B, S, p, nc, start[c], cnt[c], it == P.n_it - 1, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));   // the host copy of the colour starts must outlive the launches
+    b->pgs_colours = ncol;
+    return DEM_OK;
+}
+
 dem_status dem_launch_step(dem_bed* b) {
     const bool resort = b->g_resort && b->steps % b->resort_every == 0;
     const int p = (int)(b->steps & 1);
     if (resort) CK(cudaGraphLaunch(b->g_resort, b->stream));
     CK(cudaGraphLaunch(b->g[p][0], b->stream));
-    if (b->g[p][1]) CK(cudaGraphLaunch(b->g[p][1], b->stream));
+    if (b->P.solver && b->P.n > 0 && b->P.n_it > 0) {
+        dem_status st = pgs_solve(b, p);
+        if (st != DEM_OK) return st;
+    } else if (b->g[p][1]) CK(cudaGraphLaunch(b->g[p][1], b->stream));
     if (b->g[p][2]) CK(cudaGraphLaunch(b->g[p][2], b->stream));
     b->steps++;
     return DEM_OK;
@@ -749,7 +821,10 @@ extern "C" dem_status dem_step(dem_bed* b, int32_t nsteps) {
             if (resort) CK(cudaGraphLaunch(b->g_resort, b->stream));
             CK(cudaGraphLaunch(b->g[p][0], b->stream));
             CK(cudaEventRecord(take_event(b), b->stream));
-            if (b->g[p][1]) CK(cudaGraphLaunch(b->g[p][1], b->stream));
+            if (b->P.solver && b->P.n > 0 && b->P.n_it > 0) {
+                dem_status st = pgs_solve(b, p);
+                if (st != DEM_OK) return st;
+            } else if (b->g[p][1]) CK(cudaGraphLaunch(b->g[p][1], b->stream));
             CK(cudaEventRecord(take_event(b), b->stream));
             if (b->g[p][2]) CK(cudaGraphLaunch(b->g[p][2], b->stream));
             CK(cudaEventRecord(take_event(b), b->stream));
@@ -796,6 +871,7 @@ extern "C" dem_status dem_apply_plate_load(dem_bed* b, const int32_t* geoms, int
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(force[k])) return fail(DEM_ERR_ARG, "non-finite force");
     if (b->P.n_groups >= DEM_MAX_GROUPS) return fail(DEM_ERR_ARG, "more than %d load-driven groups", DEM_MAX_GROUPS);
+    if (b->P.solver) return fail(DEM_ERR_ARG, "the Gauss-Seidel solver does not take load-driven groups");
     const int bed0 = group_bed_nit(b, geoms[0]);
     for (int k = 0; k < count; ++k) {
         const int g = geoms[k];
@@ -1001,6 +1077,8 @@ extern "C" dem_status dem_get_info(dem_bed* b, dem_info* out) {
     out->n_beds = b->nbeds;
     out->lanes = b->P.lanes;
     out->resort_every = b->resort_every;
+    out->solver = b->P.solver;
+    out->colours = b->P.solver ? b->pgs_colours : 0;
     if (b->steps > 0 && b->P.n > 0) {
         const int p = (int)((b->steps - 1) & 1);
         int a = 0, g = 0;
@@ -1056,6 +1134,10 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
         return fail(DEM_ERR_ARG, "invalid solver or material settings");
     const int lanes = d->lanes >= 0 ? d->lanes : b->P.lanes;
     if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return fail(DEM_ERR_ARG, "bad lanes");
+    const int solver = d->solver >= 0 ? d->solver : b->P.solver;
+    if (solver != 0 && solver != 1) return fail(DEM_ERR_ARG, "bad solver");
+    if (solver && b->P.n_groups > 0)
+        return fail(DEM_ERR_ARG, "the Gauss-Seidel solver does not take load-driven groups");
     CK(cudaSetDevice(b->dev));
     SimParams& P = b->P;
     const float scale = d->dt / P.dt;
@@ -1080,6 +1162,7 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
     P.mu_r = d->mu_r;
     P.gx = d->gravity[0]; P.gy = d->gravity[1]; P.gz = d->gravity[2];
     P.lanes = lanes;
+    P.solver = solver;
     CK(cudaMemcpyAsync(b->B.lv, b->levels.data(), b->levels.size() * sizeof(LevelGrid), cudaMemcpyHostToDevice,
                        b->stream));
     CK(cudaStreamSynchronize(b->stream));

@@ -42,6 +42,10 @@ struct dem_bed {
     int64_t t_steps = 0;
     // reverse-mode differentiation state (adjoint.cu), created on first use
     AdjointState* adj = nullptr;
+    // coloured projected Gauss-Seidel buffers (solver 1), created on first use
+    PgsBuf pgs{};
+    int64_t pgs_cap = 0;
+    int pgs_colours = 0;        // colours of the last PGS step
 };
 
 // error reporting through dem_last_error(); printf-style message

@@ -95,6 +95,7 @@ struct SimParams {
     int lanes;          // sweep layout: 0 two-pass, else threads per body in one kernel
     int nit_uniform;    // 1 when every bed takes n_it sweeps
     int n_groups;       // load-driven groups
+    int solver;         // 0 projected Jacobi (mass splitting), 1 coloured projected Gauss-Seidel
 };
 
 // Device pointers of one bed.  The two warm-start generations (parity of the
@@ -188,6 +189,30 @@ int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int n
 int launch_integrate(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s);
 // contacts of load-driven groups at sweep it (before the sweep's body updates)
 int launch_group_contacts(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s);
+
+// coloured projected Gauss-Seidel (solver 1): colouring and colour sweeps.
+// Unified contact index u: u < nc sphere-sphere contact u, else sphere-geometry
+// contact u - nc.
+struct PgsBuf {
+    int* col;                   // [cap] colour, -1 while uncoloured
+    unsigned long long* prio;   // [cap] priority (mix of the contact key)
+    unsigned long long* key;    // [cap] contact key (tie-break)
+    int* gbody;                 // [max_geo] body of each sphere-geometry contact
+    int* remaining;             // [1] uncoloured contacts
+    int* ncol;                  // [1] colours used
+    int* colcnt;                // [PGS_MAX_COLOURS] contacts per colour
+    int* colstart;              // [PGS_MAX_COLOURS]
+    int* colfill;               // [PGS_MAX_COLOURS]
+    int* list;                  // [cap] contacts ordered by colour
+};
+#define PGS_MAX_COLOURS 128
+int launch_pgs_prepare(const SimParams& P, const DevBuf& B, const PgsBuf& S, int parity, int nc, int ngc,
+                       cudaStream_t s);
+int launch_pgs_round(const SimParams& P, const DevBuf& B, const PgsBuf& S, int parity, int nc, int ngc,
+                     cudaStream_t s);
+int launch_pgs_bucket(const PgsBuf& S, int total, bool fill, cudaStream_t s);
+int launch_pgs_colour(const SimParams& P, const DevBuf& B, const PgsBuf& S, int parity, int nc, int first,
+                      int count, bool last, cudaStream_t s);
 int launch_resort(const SimParams& P, const DevBuf& B, cudaStream_t s);
 int launch_radix_sort(unsigned* key_a, int* val_a, unsigned* key_b, int* val_b, int n, int* hist,
                       int* tmp, cudaStream_t s);

@@ -112,7 +112,9 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         const float la = ra - 0.5f * delta, lb = rb - 0.5f * delta;
         const float dstar = 2.0f * ra * rb / (ra + rb);   // (1/d_a + 1/d_b)^-1, also r_eff
         const float kn = P.kn_scale * P.Estar_ss * sqrtf(dstar) / 3.0f;
-        const float ima = na * va.w, imb = nb * vb.w, iIa = na * wa.w, iIb = nb * wb.w;
+        // Jacobi splits a body's mass over its contacts; Gauss-Seidel does not
+        const int sa = P.solver ? 1 : na, sb = P.solver ? 1 : nb;
+        const float ima = sa * va.w, imb = sb * vb.w, iIa = sa * wa.w, iIb = sb * wb.w;
         const float Gv = dot(n, f3(va) - f3(vb));
         const RowC rc = spook_row(P, delta, kn, Gv, ima + imb, la * la * iIa + lb * lb * iIb, iIa + iIb);
         B.rec[3 * (size_t)c + 0] = make_float4(n.x, n.y, n.z, rc.invDn);
@@ -149,7 +151,8 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         const float3 vgp = make_float3((float)G.v[0], (float)G.v[1], (float)G.v[2]) + cross(wg, lever);
         const float dstar = 2.0f * ra;   // flat primitive: d_b -> infinity
         const float kn = P.kn_scale * G.Estar * sqrtf(dstar) / 3.0f;
-        const float ima = na * va.w, iIa = na * wa.w;
+        const int sa = P.solver ? 1 : na;
+        const float ima = sa * va.w, iIa = sa * wa.w;
         const float Gv = dot(n, f3(va) - vgp);
         const RowC rc = spook_row(P, delta, kn, Gv, ima, la * la * iIa, iIa);
         // side b's split inverse mass: zero for kinematic geometry; a load-driven
@@ -407,7 +410,8 @@ __global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = !*B.err;
     if (i < P.n && ok) {
-        const int src = body_nit(P, B, i) & 1;   // the bed's final iterate
+        // the bed's final iterate (Gauss-Seidel updates one buffer in place)
+        const int src = P.solver ? 0 : body_nit(P, B, i) & 1;
         const float4 v = B.vw[src][i].v, w = B.vw[src][i].w;
         if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(w.x) && isfinite(w.y) &&
               isfinite(w.z)))
@@ -626,6 +630,184 @@ __global__ void __launch_bounds__(SV_T) k_group_contacts(SimParams P, DevBuf B, 
 int launch_group_contacts(const SimParams& P, const DevBuf& B, int parity, int it, cudaStream_t s) {
     if (P.n_groups == 0) return 0;
     k_group_contacts<<<64, SV_T, 0, s>>>(P, B, parity, it);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// Coloured projected Gauss-Seidel
+// ---------------------------------------------------------------------------
+static int sm_count();
+// SplitMix64 finaliser (Steele, Lea and Flood 2014; Vigna): a contact's
+// priority is the mix of its key (lower stable id, higher stable id) or
+// (stable id, -(primitive + 1)); higher priority colours first.
+static __device__ __forceinline__ unsigned long long pgs_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void __launch_bounds__(SV_T) k_pgs_prepare(SimParams P, DevBuf B, PgsBuf S, int p, int nc, int ngc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < P.n)   // body of every sphere-geometry contact
+        for (int k = B.geo_start[p][t]; k < B.geo_start[p][t + 1]; ++k) S.gbody[k] = t;
+    if (t == 0) {
+        *S.remaining = nc + ngc;
+        *S.ncol = 0;
+    }
+    if (t < PGS_MAX_COLOURS) {
+        S.colcnt[t] = 0;
+        S.colfill[t] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(SV_T) k_pgs_keys(SimParams P, DevBuf B, PgsBuf S, int p, int nc, int ngc) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nc + ngc) return;
+    unsigned long long key;
+    if (u < nc) {
+        const int ia = B.id[B.c_self[u]], ib = B.id[B.c_other[u]];
+        const int lo = min(ia, ib), hi = max(ia, ib);
+        key = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
+    } else {
+        const int k = u - nc;
+        key = ((unsigned long long)(unsigned)B.id[S.gbody[k]] << 32) | (unsigned)(-(B.g_key[p][k] + 1));
+    }
+    S.key[u] = key;
+    S.prio[u] = pgs_mix(key);
+    S.col[u] = -1;
+}
+
+static __device__ __forceinline__ bool pgs_before(const PgsBuf& S, int m, int u) {
+    const unsigned long long pm = S.prio[m], pu = S.prio[u];
+    return pm != pu ? pm > pu : S.key[m] < S.key[u];
+}
+
+// One Jones-Plassmann round: an uncoloured contact whose higher-priority
+// neighbours (contacts sharing a body) are all coloured takes the smallest
+// colour none of them has -- the greedy colouring in priority order.
+__global__ void __launch_bounds__(SV_T) k_pgs_round(SimParams P, DevBuf B, PgsBuf S, int p, int nc, int ngc) {
+    volatile int* col = S.col;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nc + ngc; u += gridDim.x * blockDim.x) {
+        if (col[u] >= 0) continue;
+        int body[2];
+        if (u < nc) { body[0] = B.c_self[u]; body[1] = B.c_other[u]; }
+        else { body[0] = S.gbody[u - nc]; body[1] = -1; }
+        unsigned long long used[2] = {0ull, 0ull};
+        bool blocked = false;
+        for (int s2 = 0; s2 < 2 && !blocked; ++s2) {
+            const int i = body[s2];
+            if (i < 0) continue;
+            for (int e = B.inc_start[i]; e < B.inc_start[i + 1] && !blocked; ++e) {
+                const int m = B.inc[e].x & 0x7fffffff;
+                if (m == u) continue;
+                const int cm = col[m];
+                if (cm >= 0) used[cm >> 6] |= 1ull << (cm & 63);
+                else blocked = pgs_before(S, m, u);
+            }
+            for (int k = B.geo_start[p][i]; k < B.geo_start[p][i + 1] && !blocked; ++k) {
+                const int m = nc + k;
+                if (m == u) continue;
+                const int cm = col[m];
+                if (cm >= 0) used[cm >> 6] |= 1ull << (cm & 63);
+                else blocked = pgs_before(S, m, u);
+            }
+        }
+        if (blocked) continue;
+        const int c = ~used[0] ? __ffsll((long long)~used[0]) - 1 : (~used[1] ? 64 + __ffsll((long long)~used[1]) - 1 : -1);
+        if (c < 0) {
+            set_flag(B.err, DEM_FLAG_CAPACITY);   // more than PGS_MAX_COLOURS colours
+            col[u] = PGS_MAX_COLOURS - 1;
+        } else {
+            col[u] = c;
+        }
+        atomicSub(S.remaining, 1);
+        atomicMax(S.ncol, (c < 0 ? PGS_MAX_COLOURS - 1 : c) + 1);
+    }
+}
+
+// fill = false: count per colour; true: list the contacts by colour
+__global__ void __launch_bounds__(SV_T) k_pgs_bucket(PgsBuf S, int total, int fill) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= total) return;
+    const int c = S.col[u];
+    if (!fill) atomicAdd(&S.colcnt[c], 1);
+    else S.list[S.colstart[c] + atomicAdd(&S.colfill[c], 1)] = u;
+}
+
+// Contacts of one colour: each update's impulse change goes into its bodies at
+// once; no two contacts of a colour share a body.  Iterate buffer 0 in place.
+__global__ void __launch_bounds__(SV_T) k_pgs_colour(SimParams P, DevBuf B, PgsBuf S, int p, int nc, int first,
+                                                    int count, int last) {
+    if (*B.err) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        const int u = S.list[first + t];
+        float3 La = make_float3(0.f, 0.f, 0.f), Aa = La, Lb = La, Ab = La;
+        if (u < nc) {
+            const int c = u, a = B.c_self[c], b = B.c_other[c];
+            const float4 r0 = B.rec[3 * (size_t)c], r1 = B.rec[3 * (size_t)c + 1], r2 = B.rec[3 * (size_t)c + 2];
+            const float4 l0 = B.lamA[0][c];
+            const float2 l1 = B.lamB[0][c];
+            VW A = B.vw[0][a], Bv = B.vw[0][b];
+            const Upd u2 = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, f3(A.v) - f3(Bv.v), f3(A.w),
+                                          f3(Bv.w), P.eps_reg);
+            const float3 n = f3(r0);
+            const float3 dpr = u2.pr - make_float3(l0.w, l1.x, l1.y);
+            add_impulse(n, u2.t1, u2.t2, r2.x, u2.pn - l0.x, u2.pt1 - l0.y, u2.pt2 - l0.z, dpr, false, La, Aa);
+            add_impulse(n, u2.t1, u2.t2, r2.y, u2.pn - l0.x, u2.pt1 - l0.y, u2.pt2 - l0.z, dpr, true, Lb, Ab);
+            A.v = make_float4(A.v.x + A.v.w * La.x, A.v.y + A.v.w * La.y, A.v.z + A.v.w * La.z, A.v.w);
+            A.w = make_float4(A.w.x + A.w.w * Aa.x, A.w.y + A.w.w * Aa.y, A.w.z + A.w.w * Aa.z, A.w.w);
+            Bv.v = make_float4(Bv.v.x + Bv.v.w * Lb.x, Bv.v.y + Bv.v.w * Lb.y, Bv.v.z + Bv.v.w * Lb.z, Bv.v.w);
+            Bv.w = make_float4(Bv.w.x + Bv.w.w * Ab.x, Bv.w.y + Bv.w.w * Ab.y, Bv.w.z + Bv.w.w * Ab.z, Bv.w.w);
+            B.vw[0][a] = A;
+            B.vw[0][b] = Bv;
+            B.lamA[0][c] = make_float4(u2.pn, u2.pt1, u2.pt2, u2.pr.x);
+            B.lamB[0][c] = make_float2(u2.pr.y, u2.pr.z);
+            if (last) write_world(B.lamW[p], c, n, u2);
+        } else {
+            const int k = u - nc, a = S.gbody[k];
+            const float4* r = B.grec + 6 * (size_t)k;
+            const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+            const float4 l0 = B.glamA[0][k];
+            const float2 l1 = B.glamB[0][k];
+            VW A = B.vw[0][a];
+            const Upd u2 = contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, f3(A.v) - f3(r3), f3(A.w), f3(r4),
+                                          P.eps_reg);
+            const float3 n = f3(r0);
+            const float3 dpr = u2.pr - make_float3(l0.w, l1.x, l1.y);
+            add_impulse(n, u2.t1, u2.t2, r2.x, u2.pn - l0.x, u2.pt1 - l0.y, u2.pt2 - l0.z, dpr, false, La, Aa);
+            A.v = make_float4(A.v.x + A.v.w * La.x, A.v.y + A.v.w * La.y, A.v.z + A.v.w * La.z, A.v.w);
+            A.w = make_float4(A.w.x + A.w.w * Aa.x, A.w.y + A.w.w * Aa.y, A.w.z + A.w.w * Aa.z, A.w.w);
+            B.vw[0][a] = A;
+            B.glamA[0][k] = make_float4(u2.pn, u2.pt1, u2.pt2, u2.pr.x);
+            B.glamB[0][k] = make_float2(u2.pr.y, u2.pr.z);
+            if (last) write_world(B.glamW[p], k, n, u2);
+        }
+    }
+}
+
+int launch_pgs_prepare(const SimParams& P, const DevBuf& B, const PgsBuf& S, int parity, int nc, int ngc,
+                       cudaStream_t s) {
+    k_pgs_prepare<<<nblk(std::max(P.n, PGS_MAX_COLOURS), SV_T), SV_T, 0, s>>>(P, B, S, parity, nc, ngc);
+    k_pgs_keys<<<nblk(nc + ngc, SV_T), SV_T, 0, s>>>(P, B, S, parity, nc, ngc);
+    return 2;
+}
+
+int launch_pgs_round(const SimParams& P, const DevBuf& B, const PgsBuf& S, int parity, int nc, int ngc,
+                     cudaStream_t s) {
+    k_pgs_round<<<std::max(1, std::min(nblk(nc + ngc, SV_T), 8 * sm_count())), SV_T, 0, s>>>(P, B, S, parity, nc,
+                                                                                            ngc);
+    return 1;
+}
+
+int launch_pgs_bucket(const PgsBuf& S, int total, bool fill, cudaStream_t s) {
+    k_pgs_bucket<<<nblk(total, SV_T), SV_T, 0, s>>>(S, total, fill ? 1 : 0);
+    return 1;
+}
+
+int launch_pgs_colour(const SimParams& P, const DevBuf& B, const PgsBuf& S, int parity, int nc, int first,
+                      int count, bool last, cudaStream_t s) {
+    k_pgs_colour<<<std::max(1, std::min(nblk(count, SV_T), 8 * sm_count())), SV_T, 0, s>>>(P, B, S, parity, nc,
+                                                                                           first, count, last);
     return 1;
 }
 

@@ -57,7 +57,7 @@ class dem_bed_desc(C.Structure):
                 ("geom", C.POINTER(dem_geom)), ("contact_capacity", C.c_int64),
                 ("resort_every", C.c_int32), ("level_ratio", C.c_float), ("lanes", C.c_int32),
                 ("alloc", ALLOC_FN),
-                ("free_fn", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("free_fn", FREE_FN), ("alloc_ctx", C.c_void_p), ("solver", C.c_int32)]
 
 
 class dem_info(C.Structure):
@@ -65,7 +65,7 @@ class dem_info(C.Structure):
                 ("contacts", C.c_int64), ("geom_contacts", C.c_int64), ("steps", C.c_int64),
                 ("contact_capacity", C.c_int64), ("kernels_per_step", C.c_int32),
                 ("kernels_per_resort", C.c_int32), ("n_beds", C.c_int32), ("lanes", C.c_int32),
-                ("resort_every", C.c_int32)]
+                ("resort_every", C.c_int32), ("solver", C.c_int32), ("colours", C.c_int32)]
 
 
 _lib = None
@@ -192,7 +192,7 @@ class _TorchAllocator:
 def _make_desc(x, r, keep, *, v=None, w=None, geoms=(), rho=2600.0, E=1e9, nu=0.15, mu_t=0.5,
                mu_r=0.02, e_H=1.25, damp_steps=4.5, dt=1e-5, n_it=100, gravity=(0.0, 0.0, -9.81),
                kn_scale=1.0, eps_reg=1e-6, delta_floor=0.0, inv_mass=None, inv_inertia=None,
-               contact_capacity=0, resort_every=0, level_ratio=0.0, lanes=0):
+               contact_capacity=0, resort_every=0, level_ratio=0.0, lanes=0, solver=0):
     """A dem_bed_desc for one bed; arrays that must outlive the call go to keep."""
     x = _input(x, np.float64, (-1, 3))
     r = _input(r, np.float32, (-1,))
@@ -222,6 +222,7 @@ def _make_desc(x, r, keep, *, v=None, w=None, geoms=(), rho=2600.0, E=1e9, nu=0.
     d.resort_every = int(resort_every)
     d.level_ratio = float(level_ratio)
     d.lanes = int(lanes)
+    d.solver = int(solver)
     return d, n, geoms
 
 
@@ -342,12 +343,13 @@ class Bed:
         return a.value, j.value, s.value
 
     def set_params(self, *, dt, n_it, mu_t, mu_r, damp_steps=4.5, e_H=1.25, gravity=(0.0, 0.0, -9.81),
-                   kn_scale=1.0, eps_reg=1e-6, lanes=0):
-        """Change solver and material settings between steps (dem_set_params)."""
+                   kn_scale=1.0, eps_reg=1e-6, lanes=0, solver=-1):
+        """Change solver and material settings between steps (dem_set_params);
+        solver -1 keeps the current one."""
         d = dem_bed_desc()
         d.dt, d.n_it, d.mu_t, d.mu_r, d.damp_steps, d.e_H = dt, int(n_it), mu_t, mu_r, damp_steps, e_H
         d.gravity = (C.c_float * 3)(*map(float, gravity))
-        d.kn_scale, d.eps_reg, d.lanes = kn_scale, eps_reg, int(lanes)
+        d.kn_scale, d.eps_reg, d.lanes, d.solver = kn_scale, eps_reg, int(lanes), int(solver)
         _check(self.lib.dem_set_params(self._handle, C.byref(d)))
         self.dt = dt
         self.params = dict(dt=dt, n_it=int(n_it), mu_t=mu_t, mu_r=mu_r, damp_steps=damp_steps, e_H=e_H,

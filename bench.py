@@ -592,6 +592,63 @@ def run_triaxial(args):
                 sweep_layout=info.lanes, **prep)
 
 
+SOLVER_NITS = (5, 10, 20, 40, 74, 150, 300, 600)
+
+
+def run_solvers(args):
+    """Jacobi (mass splitting) against coloured projected Gauss-Seidel on the
+    settled refined bed: one step from the same warm-started state for each
+    N_it, relative error of all contact impulses (normal, tangential, rolling)
+    against a converged solve (PGS, 1500 sweeps), and the iterations each needs
+    to reach a tolerance, next to Eq. 8's N_it = 74."""
+    import torch
+    from paper_2501_05300_gb300 import dem
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    spec = beds.refined_sinkage_bed()
+    bed, top = settle_and_place(dem, spec, args.settle, 0)
+    bed.apply_plate_velocity(spec.plate, (0.0, 0.0, -PLATE_V))
+    bed.step(20)
+    start = bed.save_checkpoint()
+    m = spec.material
+
+    def one(solver, nit):
+        bed.restore_checkpoint(start)
+        bed.set_params(dt=DT, n_it=nit, mu_t=m.mu_t, mu_r=m.mu_r, lanes=0, solver=solver)
+        bed.step(1)          # untimed: graphs and buffers in place
+        bed.restore_checkpoint(start)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bed.step(1)
+        bed.sync()
+        el = time.perf_counter() - t0
+        info = bed.info()
+        return bed.read_contacts()[2].astype(np.float64), el, info.colours
+
+    ref, _, _ = one(1, 1500)
+    nref = np.linalg.norm(ref)
+    table = {"jacobi": [], "pgs": []}
+    colours = 0
+    for name, solver in (("jacobi", 0), ("pgs", 1)):
+        for nit in SOLVER_NITS:
+            v, el, col = one(solver, nit)
+            colours = max(colours, col)
+            table[name].append({"n_it": nit, "rel_error": float(np.linalg.norm(v - ref) / nref), "step_ms": el * 1e3})
+
+    def needed(rows, tol):
+        for r in rows:
+            if r["rel_error"] <= tol:
+                return r["n_it"]
+        return None
+
+    info = bed.info()
+    bed.free_checkpoint(start)
+    bed.close()
+    return dict(table=table, colours=colours, particles=info.n, contacts=info.contacts + info.geom_contacts,
+                iterations_to_1e_2={k: needed(v, 1e-2) for k, v in table.items()},
+                iterations_to_1e_3={k: needed(v, 1e-3) for k, v in table.items()}, eq8_n_it=N_IT)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -602,6 +659,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="the 36-bed batched-vs-sequential comparison")
     ap.add_argument("--fine", action="store_true", help="the ~4 M-sphere homogeneous fine bed")
     ap.add_argument("--fine-small", action="store_true", help="with --fine: a quarter of the footprint (~1 M)")
+    ap.add_argument("--solvers", action="store_true",
+                    help="Jacobi against coloured Gauss-Seidel: iterations to tolerance on the refined bed")
     ap.add_argument("--triaxial", action="store_true",
                     help="adjoint cost and gradient check on the 50k triaxial cell")
     ap.add_argument("--triax-steps", type=int, default=TRIAX_STEPS, help="with --triaxial: window length")
@@ -642,6 +701,16 @@ def main():
                           "higher_is_better": True, "steps": args.steps, "data": "synthetic",
                           "config": {"workload": "36 refined beds (6x6 grid), one object vs one by one",
                                      **{k: v for k, v in r.items() if k != "speedup"}}}))
+        return
+    if args.solvers:
+        r = run_solvers(args)
+        print(json.dumps({"metric": "Jacobi sweeps / coloured Gauss-Seidel sweeps to 1e-3", "unit": "x",
+                          "value": (r["iterations_to_1e_3"]["jacobi"] / r["iterations_to_1e_3"]["pgs"]
+                                    if r["iterations_to_1e_3"]["jacobi"] and r["iterations_to_1e_3"]["pgs"]
+                                    else None),
+                          "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": WORKLOAD + "; one step from the settled state, relative error of "
+                                                 "all contact impulses against 1500 Gauss-Seidel sweeps", **r}}))
         return
     if args.triaxial:
         r = run_triaxial(args)

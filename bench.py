@@ -451,14 +451,14 @@ def _servo(bed, walls, target, vmax):
     return sig, L
 
 
-def prepare_triaxial(dem, lanes=0, n=TRIAX_N, seed=2505, max_steps=8000):
+def prepare_triaxial(dem, lanes=0, n=TRIAX_N, seed=2505, max_steps=8000, spec=None):
     """Isotropic consolidation, then the start of drained shearing.
     Consolidation (Sec. 3.1 generation friction mu_t 0.1, mu_r 0.01, no
     gravity, dt 5e-5 from Eq. 9 at 100 kPa, 60 sweeps): all six walls servo to
     100 kPa.  Shearing (test friction, dt 1e-5, N_it from Eq. 8 with n_d =
     h/d): the platen moves down at strain rate 0.5/s while the side walls keep
     servoing to 100 kPa for 300 steps."""
-    spec = beds.triaxial_cell(n, seed=seed)
+    spec = spec if spec is not None else beds.triaxial_cell(n, seed=seed)
     m = spec.material
     bed = dem.Bed(spec.x, spec.r, geoms=spec.geoms, rho=m.rho, mu_t=0.1, mu_r=0.01, n_it=60, dt=5e-5,
                   gravity=(0.0, 0.0, 0.0), lanes=lanes)
@@ -649,6 +649,51 @@ def run_solvers(args):
                 iterations_to_1e_3={k: needed(v, 1e-3) for k, v in table.items()}, eq8_n_it=N_IT)
 
 
+def run_calibrate(args, max_iter=8, rtol=0.005):
+    """Gradient-driven calibration: the refined triaxial cell's friction
+    coefficient mu_t is adjusted until its mean deviatoric stress over the
+    400-step window equals the fine cell's (the same protocol), by Newton steps
+    on that one parameter with dJ/dmu_t from the adjoint."""
+    import torch
+    from paper_2501_05300_gb300 import dem
+    from paper_2501_05300_gb300.adjoint import CellGeometry, deviatoric_stress, geom_forces
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    lanes = max(args.lanes, 0)
+    steps, every = args.triax_steps, args.triax_ckpt
+    fine, fprep = prepare_triaxial(dem, lanes=lanes)
+    fine.step(args.warmup)
+    fcell = CellGeometry.from_bed(fine)
+    target = float(deviatoric_stress(torch.from_numpy(fine.record(steps, steps)), fcell).mean())
+    n_fine = fine.n
+    fine.close()
+    bed, prep = prepare_triaxial(dem, lanes=lanes, spec=beds.triaxial_refined_cell())
+    bed.step(args.warmup)
+    start = bed.save_checkpoint()
+    cell = CellGeometry.from_bed(bed)
+    theta = [1.0, 0.5, 0.02]
+    hist = []
+    t0 = time.perf_counter()
+    for k in range(max_iter):
+        bed.restore_checkpoint(start)
+        th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        F = geom_forces(bed, th, steps, every)
+        J = deviatoric_stress(F, cell).mean()
+        J.backward()
+        g = float(th.grad[1])
+        hist.append({"mu_t": theta[1], "J": float(J.detach()), "dJ_dmu_t": g})
+        if abs(float(J.detach()) - target) <= rtol * abs(target) or g == 0.0:
+            break
+        theta[1] = float(np.clip(theta[1] - (float(J.detach()) - target) / g, 0.02, 2.0))
+    el = time.perf_counter() - t0
+    n_ref = bed.n
+    bed.free_checkpoint(start)
+    bed.close()
+    return dict(target_Pa=target, fine_particles=n_fine, refined_particles=n_ref, history=hist,
+                iterations=len(hist), mu_t=hist[-1]["mu_t"], rel_mismatch=abs(hist[-1]["J"] - target) / abs(target),
+                seconds_per_gradient=el / len(hist), window_steps=steps)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -659,6 +704,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="the 36-bed batched-vs-sequential comparison")
     ap.add_argument("--fine", action="store_true", help="the ~4 M-sphere homogeneous fine bed")
     ap.add_argument("--fine-small", action="store_true", help="with --fine: a quarter of the footprint (~1 M)")
+    ap.add_argument("--calibrate", action="store_true",
+                    help="gradient-driven calibration of the refined triaxial cell against the fine one")
     ap.add_argument("--solvers", action="store_true",
                     help="Jacobi against coloured Gauss-Seidel: iterations to tolerance on the refined bed")
     ap.add_argument("--triaxial", action="store_true",
@@ -701,6 +748,15 @@ def main():
                           "higher_is_better": True, "steps": args.steps, "data": "synthetic",
                           "config": {"workload": "36 refined beds (6x6 grid), one object vs one by one",
                                      **{k: v for k, v in r.items() if k != "speedup"}}}))
+        return
+    if args.calibrate:
+        r = run_calibrate(args)
+        print(json.dumps({"metric": "calibration mismatch |J - J_fine| / J_fine", "value": r["rel_mismatch"],
+                          "unit": "1", "higher_is_better": False, "n_gpus": 1, "dtype": "f32",
+                          "data": "synthetic",
+                          "config": {"workload": "mean deviatoric stress of a refined triaxial cell (coarse lower "
+                                                 "half) matched to the 50k fine cell by Newton steps on mu_t with "
+                                                 "adjoint gradients", **r}}))
         return
     if args.solvers:
         r = run_solvers(args)

@@ -367,3 +367,17 @@ def triaxial_cell(n=50_000, rmin=2.5e-3, rmax=3.0e-3, seed=2505, gap=0.01, squee
     return Bed(x, r, cell_walls(lo, hi, v_top), mat, plate=PLATEN,
                name=f"triaxial cell, {n} spheres r~U[{rmin * 1e3:g},{rmax * 1e3:g}] mm",
                box=tuple(map(float, hi - lo)))
+
+
+def triaxial_refined_cell(side=0.2, r_fine=2.75e-3, growth=2.0, seed=2506, gap=0.01):
+    """A triaxial cell of the fine cell's size whose lower half holds spheres
+    `growth` times larger (10% spread): a two-layer refined sample (Sec. 2.1)
+    inside the six walls of a box cell (Sec. 3.2)."""
+    x, r = layered_bed(side, side, [(r_fine * growth, side / 2), (r_fine, side / 2)], spread=0.1, seed=seed,
+                       gap=gap)
+    rr = r.astype(np.float64)[:, None]
+    lo, hi = (x - rr).min(0), (x + rr).max(0)
+    mat = Material(rho=2600.0, mu_t=0.5, mu_r=0.02)
+    return Bed(x, r, cell_walls(lo, hi), mat, plate=PLATEN,
+               name=f"refined triaxial cell, {len(r)} spheres r {r_fine * 1e3:g}/{r_fine * growth * 1e3:g} mm",
+               box=tuple(map(float, hi - lo)))

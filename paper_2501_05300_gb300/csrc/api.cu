@@ -547,6 +547,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
         o.mu_t = G.mu_t;
         o.mu_r = G.mu_r;
         o.grp = -1;
+        for (int k = 0; k < 3; ++k) { o.fc[k] = (float)o.c[k]; o.fn[k] = (float)o.R[3 * k + 2]; }
         o.bound = (float)(G.type == DEM_GEOM_BOX ? std::sqrt(G.he[0] * G.he[0] + G.he[1] * G.he[1] + G.he[2] * G.he[2])
                                                  : std::sqrt(G.he[0] * G.he[0] + G.he[2] * G.he[2])) * 1.0001f;
     }

@@ -12,7 +12,12 @@
 // Contact predicate (exact): |x_a - x_b|^2 < (r_a + r_b)^2 evaluated in IEEE
 // double from the double centres, as (dx^2 + dy^2) + dz^2 with every product
 // and sum rounded separately (no fused multiply-add).  An FP32 pre-test with a
-// tolerance that covers the rounding of the FP32 copies rejects the far pairs.
+// tolerance tol that covers the rounding of the FP32 copies and of the FP32
+// arithmetic settles all but a thin band of pairs: d_f32 >= r_a + r_b + tol
+// rejects, d_f32 < r_a + r_b - 2 tol accepts (the double distance is then below
+// r_a + r_b - tol, and tol is tens of FP32 ulps of r_a + r_b, far above the
+// double predicate's rounding), and only the band in between is decided by
+// the FP64 predicate.  The contact set is the exact predicate's either way.
 #include "dem_internal.cuh"
 
 #define BP_T 128
@@ -20,11 +25,12 @@
 #include "geometry.cuh"
 
 // FP32 pre-test: can the sphere touch the primitive at all?
+// (FP32 copies of the pose: on this part every FP64 instruction, a conversion
+// included, costs a multiple of its FP32 counterpart)
 static __device__ __forceinline__ bool geom_near(const GeomDev& g, float4 p, float tol) {
-    float cx = (float)g.c[0], cy = (float)g.c[1], cz = (float)g.c[2];
-    float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
+    float dx = p.x - g.fc[0], dy = p.y - g.fc[1], dz = p.z - g.fc[2];
     if (g.type == DEM_GEOM_PLANE) {
-        float s = (float)g.R[2] * dx + (float)g.R[5] * dy + (float)g.R[8] * dz;
+        float s = g.fn[0] * dx + g.fn[1] * dy + g.fn[2] * dz;
         return s < p.w + tol;
     }
     float reach = g.bound + p.w + tol;
@@ -145,12 +151,19 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
                 const float4 pj = B.cell_pos[k];
                 const float R = pi.w + pj.w + P.tol;
                 const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                if (dx * dx + dy * dy + dz * dz < R * R) {
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 < R * R) {
                     j = B.cell_body[k];
                     if (j != i) {
                         idj = B.id[j];
                         // same level: the lower id owns the pair
-                        if (!(l == li && idj < idi)) hit = exact_pair(xi, B.pos[j]);
+                        if (!(l == li && idj < idi)) {
+                            // FP32 accept: the double distance is below r_a + r_b - tol
+                            // here, far inside the exact predicate's rounding; only
+                            // the band around contact takes the FP64 test
+                            const float Rin = fmaxf(pi.w + pj.w - 2.0f * P.tol, 0.0f);
+                            hit = d2 < Rin * Rin || exact_pair(xi, B.pos[j]);
+                        }
                     }
                 }
             }

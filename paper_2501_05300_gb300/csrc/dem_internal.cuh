@@ -66,6 +66,8 @@ struct GeomDev {
     float mu_t, mu_r;
     float bound;        // radius of a sphere around c holding the primitive (box, cylinder)
     int grp;            // load-driven rigid group the primitive belongs to, or -1
+    float fc[3];        // c and the third column of R rounded to FP32, for the
+    float fn[3];        //   FP32 pre-test (refreshed wherever c or R change)
 };
 
 // A load-driven rigid group of primitives (a plate under a normal load): it

@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p
                         Rn[3 * a + b] = Rot[a][0] * G.R[b] + Rot[a][1] * G.R[3 + b] + Rot[a][2] * G.R[6 + b];
                 for (int k = 0; k < 9; ++k) G.R[k] = Rn[k];
             }
+            for (int k = 0; k < 3; ++k) { G.fc[k] = (float)G.c[k]; G.fn[k] = (float)G.R[3 * k + 2]; }
         }
         *B.resorted = 0;
     }

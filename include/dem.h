@@ -95,7 +95,11 @@ typedef struct dem_bed_desc {
     int32_t resort_every;       /* Morton re-sort period in steps; 0 = 20 */
     float level_ratio;          /* radius ratio per grid level; 0 = 2 */
     int32_t lanes;              /* Jacobi sweep layout: 0 = contact pass + body pass (default);
-                                   1, 2, 4, 8 = one kernel with that many threads per particle */
+                                   1, 2, 4, 8 = one kernel with that many threads per particle;
+                                   16 = resident: all sweeps of a step in one cooperative kernel,
+                                   one block per SM holding a range of bodies on chip (beds of one
+                                   n_it, Jacobi, no load-driven groups, up to ~3,500 particles per
+                                   SM; other beds take the two-pass layout) */
     dem_alloc_fn alloc;         /* optional allocator (see above) */
     dem_free_fn free_fn;
     void* alloc_ctx;
@@ -144,9 +148,9 @@ dem_status dem_create_bed(const dem_bed_desc* desc, void* stream, dem_bed** out)
 dem_status dem_create_batch(const dem_bed_desc* descs, int32_t nbeds, void* stream, dem_bed** out);
 
 /* Autotuner: times trial_steps steps (after one untimed step) of every sweep
- * layout (lanes 0, 1, 2, 4, 8), keeps the fastest, then times re-sort periods
- * 5, 10, 20, 50 and keeps the fastest.  The bed advances by those steps: call it
- * in place of warm-up steps.  Choices are returned through lanes_out and
+ * layout (lanes 0, 1, 2, 4, 8; the resident layout 16 is opt-in), keeps the
+ * fastest, then times re-sort periods 5, 10, 20, 50 and keeps the fastest.
+ * The bed advances by those steps: call it in place of warm-up steps.  Choices are returned through lanes_out and
  * resort_out (either may be NULL) and stay in effect.  Synchronises. */
 dem_status dem_autotune(dem_bed* bed, int32_t trial_steps, int32_t* lanes_out, int32_t* resort_out);
 

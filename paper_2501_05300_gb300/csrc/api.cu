@@ -439,7 +439,8 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     if (cap > (int64_t)0x3fffffff) cap = 0x3fffffff;
     P.max_contacts = (int)cap;
     P.max_geo = 2 * n + 1024;
-    P.lanes = d->lanes;   // 0: two-pass sweep; 1, 2, 4, 8: one kernel, that many threads per body
+    P.lanes = d->lanes;   // 0: two-pass sweep; 1, 2, 4, 8: one kernel, that many threads per body;
+                          // 16: resident sweep where the bed takes it, else two-pass
     P.solver = d->solver;
     if (P.solver != 0 && P.solver != 1) {
         release(b);
@@ -450,9 +451,10 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
             release(b);
             return fail(DEM_ERR_ARG, "the Gauss-Seidel solver needs the same n_it in every bed");
         }
-    if (P.lanes != 0 && P.lanes != 1 && P.lanes != 2 && P.lanes != 4 && P.lanes != 8) {
+    if (P.lanes != 0 && P.lanes != 1 && P.lanes != 2 && P.lanes != 4 && P.lanes != 8 &&
+        P.lanes != DEM_LAYOUT_RESIDENT) {
         release(b);
-        return fail(DEM_ERR_ARG, "lanes = %d is not 0, 1, 2, 4 or 8", d->lanes);
+        return fail(DEM_ERR_ARG, "lanes = %d is not 0, 1, 2, 4, 8 or 16", d->lanes);
     }
     b->levels = levels;
     P.nit_uniform = 1;
@@ -506,7 +508,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     AL(B.c_self, C); AL(B.c_pos, C); AL(B.imp, 2 * C);
     AL(B.g_key[0], GC); AL(B.g_key[1], GC); AL(B.grec, 6 * GC); AL(B.g_delta, GC);
     AL(B.glamA[0], GC); AL(B.glamA[1], GC); AL(B.glamB[0], GC); AL(B.glamB[1], GC);
-    AL(B.glamW[0], 2 * GC); AL(B.glamW[1], 2 * GC);
+    AL(B.glamW[0], 2 * GC); AL(B.glamW[1], 2 * GC); AL(B.g_body, GC); AL(B.gsh, GC);
     AL(B.geom, (size_t)std::max(P.ng, 1)); AL(B.gacc, 6 * (size_t)std::max(P.ng, 1));
     AL(B.grp, DEM_MAX_GROUPS); AL(B.gcnt, DEM_MAX_GROUPS); AL(B.gimp, 9 * DEM_MAX_GROUPS);
     AL(B.gl_list, GC); AL(B.gl_count, 1);
@@ -653,6 +655,8 @@ static int body_pre(dem_bed* b, int p) {
 static int body_jac(dem_bed* b, int p) {
     int k = 0;
     if (b->P.n == 0) return 0;
+    if (b->P.lanes == DEM_LAYOUT_RESIDENT && b->res.prog && resident_ok(b->P, nullptr))
+        return launch_resident(b->P, b->B, b->res, p, b->stream);
     for (int it = 0; it < b->P.n_it; ++it) k += launch_jacobi(b->P, b->B, p, it, b->n_active[it], b->stream);
     return k;
 }
@@ -666,6 +670,14 @@ static int body_resort(dem_bed* b, int) { return launch_resort(b->P, b->B, b->st
 
 static dem_status build_graphs(dem_bed* b) {
     dem_status st;
+    int blocks = 0;
+    if (b->P.lanes == DEM_LAYOUT_RESIDENT && resident_ok(b->P, &blocks) && !b->res.prog) {
+        // once: the blocks' progress counters
+        ResBuf R{};
+        if ((st = dalloc(b, (void**)&R.prog, 2 * (size_t)blocks * sizeof(int))) != DEM_OK) return st;
+        R.blocks = blocks;
+        b->res = R;
+    }
     for (int p = 0; p < 2; ++p) {
         int k = 0;
         if ((st = capture(b, &b->g[p][0], &k, body_pre, p)) != DEM_OK) return st;
@@ -721,6 +733,7 @@ static dem_status check_fault(dem_bed* b) {
     if (b->timing) collect_timing(b);
     if (err) {
         b->faulted = true;
+        if (err & DEM_FLAG_TIMEOUT) return fail(DEM_ERR_TIMEOUT, "a bounded wait of the resident sweep gave up");
         if (err & DEM_FLAG_CAPACITY)
             return fail(DEM_ERR_CAPACITY, "contact storage overflowed (capacity %d contacts, %d per body)",
                         b->P.max_contacts, DEM_MAX_OWN);
@@ -1134,7 +1147,8 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
         d->mu_r < 0.f || d->eps_reg < 0.f)
         return fail(DEM_ERR_ARG, "invalid solver or material settings");
     const int lanes = d->lanes >= 0 ? d->lanes : b->P.lanes;
-    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return fail(DEM_ERR_ARG, "bad lanes");
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != DEM_LAYOUT_RESIDENT)
+        return fail(DEM_ERR_ARG, "bad lanes");
     const int solver = d->solver >= 0 ? d->solver : b->P.solver;
     if (solver != 0 && solver != 1) return fail(DEM_ERR_ARG, "bad solver");
     if (solver && b->P.n_groups > 0)
@@ -1225,6 +1239,7 @@ extern "C" dem_status dem_autotune(dem_bed* b, int32_t trial_steps, int32_t* lan
     CK(cudaSetDevice(b->dev));
     dem_status st;
     // every candidate first runs one untimed step, then trial_steps timed ones
+    // (the resident layout is opt-in: measured slower than these on every bed tried)
     const int lane_opts[5] = {0, 1, 2, 4, 8};
     int best_lanes = b->P.lanes;
     float best = 1e30f;

@@ -46,6 +46,8 @@ struct dem_bed {
     PgsBuf pgs{};
     int64_t pgs_cap = 0;
     int pgs_colours = 0;        // colours of the last PGS step
+    // resident-sweep buffers (layout DEM_LAYOUT_RESIDENT), created on first use
+    ResBuf res{};
 };
 
 // error reporting through dem_last_error(); printf-style message

@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(BP_T) k_contacts_build(SimParams P, DevBuf B, 
     for (int k = 0; k < ng; ++k) {
         if (gs + k >= gcap) { set_flag(B.err, DEM_FLAG_CAPACITY); break; }
         B.g_key[parity][gs + k] = gl[k];
+        B.g_body[gs + k] = i;
         const int q = B.geom[gl[k]].grp;
         if (q >= 0) {   // a load-driven group: its split mass and its contact list
             atomicAdd(&B.gcnt[q], 1);

@@ -26,7 +26,7 @@
 #define DEM_FIX_SCALE 17592186044416.0  // 2^44: fixed-point scale of geometry impulses [N s]
 #define DEM_MAX_GROUPS 16  // load-driven rigid groups of primitives
 
-enum { DEM_FLAG_CAPACITY = 1, DEM_FLAG_NONFINITE = 2 };
+enum { DEM_FLAG_CAPACITY = 1, DEM_FLAG_NONFINITE = 2, DEM_FLAG_TIMEOUT = 4 };
 
 // one body's velocity record: 32 bytes, one memory sector per gather
 struct __align__(32) VW {
@@ -153,6 +153,8 @@ struct DevBuf {
     float4* glamA[2];
     float2* glamB[2];
     float4* glamW[2];   // [2 * max_geo]
+    int* g_body;        // [max_geo] slot of the body of each geometry contact
+    Imp* gsh;           // [max_geo] impulse share of each geometry contact on its body
     // kinematic geometry and its force accumulators
     GeomDev* geom;      // [ng]
     long long* gacc;    // [6 ng] fixed-point impulse and angular impulse
@@ -215,6 +217,18 @@ int launch_pgs_round(const SimParams& P, const DevBuf& B, const PgsBuf& S, int p
 int launch_pgs_bucket(const PgsBuf& S, int total, bool fill, cudaStream_t s);
 int launch_pgs_colour(const SimParams& P, const DevBuf& B, const PgsBuf& S, int parity, int nc, int first,
                       int count, bool last, cudaStream_t s);
+
+// Resident sweep (layout DEM_LAYOUT_RESIDENT): all sweeps of a step in one
+// cooperative kernel, one block per SM, each block keeping a contiguous range
+// of bodies on chip.
+#define DEM_LAYOUT_RESIDENT 16
+struct ResBuf {
+    int* prog;          // [2 blocks] contact and body phases each block has finished this step
+    int blocks;         // grid size (SM count)
+};
+// can the bed take the resident sweep (and with how many blocks)
+bool resident_ok(const SimParams& P, int* blocks);
+int launch_resident(const SimParams& P, const DevBuf& B, const ResBuf& R, int parity, cudaStream_t s);
 int launch_resort(const SimParams& P, const DevBuf& B, cudaStream_t s);
 int launch_radix_sort(unsigned* key_a, int* val_a, unsigned* key_b, int* val_b, int n, int* hist,
                       int* tmp, cudaStream_t s);
@@ -229,9 +243,19 @@ static __device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, 
 static __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 static __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 static __device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
-static __device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// a b + c d with one fixed fusion (the compiler may fuse such a sum either
+// way, and may choose differently in different kernels; every sweep layout must
+// round alike)
+static __device__ __forceinline__ float fma2(float a, float b, float c, float d) {
+    return __fmaf_rn(c, d, __fmul_rn(a, b));
+}
+static __device__ __forceinline__ float dot(float3 a, float3 b) { return __fmaf_rn(a.z, b.z, fma2(a.x, b.x, a.y, b.y)); }
 static __device__ __forceinline__ float3 cross(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    return make_float3(fma2(a.y, b.z, -a.z, b.y), fma2(a.z, b.x, -a.x, b.z), fma2(a.x, b.y, -a.y, b.x));
+}
+// a u + b v, component-wise with the same fusion
+static __device__ __forceinline__ float3 lin2(float a, float3 u, float b, float3 v) {
+    return make_float3(fma2(a, u.x, b, v.x), fma2(a, u.y, b, v.y), fma2(a, u.z, b, v.z));
 }
 
 // Orthonormal tangent basis (t1, t2) of a unit normal n with t2 = n x t1,

@@ -24,6 +24,7 @@
 
 #include "dem_internal.cuh"
 #include "geometry.cuh"
+#include "sweep.cuh"
 
 #define SV_T 128
 
@@ -57,24 +58,6 @@ static __device__ __forceinline__ void warm_project(float4 w0, float4 w1, float3
     const float3 pt = make_float3(w0.y, w0.z, w0.w);
     l0 = make_float4(w0.x, dot(pt, t1), dot(pt, t2), w1.x);
     l1 = make_float2(w1.y, w1.z);
-}
-
-// Impulse of a contact on the body at `side` (false = a, true = b) with arm
-// length l: linear  +-(p_n n + p_t),  angular  -l (n x p_t) +- p_r.
-static __device__ __forceinline__ void add_impulse(float3 n, float3 t1, float3 t2, float l, float pn,
-                                                   float pt1, float pt2, float3 pr, bool sideb,
-                                                   float3& accL, float3& accA) {
-    const float3 P = make_float3(pn * n.x + pt1 * t1.x + pt2 * t2.x, pn * n.y + pt1 * t1.y + pt2 * t2.y,
-                                 pn * n.z + pt1 * t1.z + pt2 * t2.z);
-    // n x p_t = pt1 t2 - pt2 t1
-    const float3 nxpt = make_float3(pt1 * t2.x - pt2 * t1.x, pt1 * t2.y - pt2 * t1.y, pt1 * t2.z - pt2 * t1.z);
-    if (!sideb) {
-        accL = accL + P;
-        accA = accA + (pr - l * nxpt);
-    } else {
-        accL = accL - P;
-        accA = accA - (pr + l * nxpt);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -195,98 +178,6 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// the canonical contact update, identical at both ends of a contact
-// ---------------------------------------------------------------------------
-struct Upd {
-    float pn, pt1, pt2;
-    float3 pr, t1, t2;
-};
-
-// G2: the tangential block of D is a full 2x2 (i11 = r1.z, i12, i22), for the
-// contacts of a load-driven group; otherwise it is r1.z times the identity
-template <bool G2 = false>
-static __device__ __forceinline__ Upd contact_update(float4 r0, float4 r1, float la, float lb, float mu_t,
-                                                     float mur, float4 l0, float2 l1, float3 dv,
-                                                     float3 wa, float3 wb, float eps_reg, float i12 = 0.f,
-                                                     float i22 = 0.f) {
-    Upd u;
-    const float3 n = f3(r0);
-    const float sig = r1.y, sig_t = eps_reg * r1.y;
-    // normal: 0 <= p_n complementary to the SPOOK row (Eq. 5)
-    const float wn = dot(n, dv) + sig * l0.x - r1.x;
-    u.pn = fmaxf(0.0f, l0.x - r0.w * wn);
-    // contact-point relative velocity: dv + w_a x (-l_a n) - w_b x (l_b n)
-    const float3 uc = dv - cross(la * wa + lb * wb, n);
-    tangent_basis(n, u.t1, u.t2);
-    float pt1, pt2;
-    if (G2) {
-        const float w1 = dot(uc, u.t1) + sig_t * l0.y, w2 = dot(uc, u.t2) + sig_t * l0.z;
-        pt1 = l0.y - (r1.z * w1 + i12 * w2);
-        pt2 = l0.z - (i12 * w1 + i22 * w2);
-    } else {
-        pt1 = l0.y - r1.z * (dot(uc, u.t1) + sig_t * l0.y);
-        pt2 = l0.z - r1.z * (dot(uc, u.t2) + sig_t * l0.z);
-    }
-    const float bt = mu_t * u.pn;
-    const float m2 = pt1 * pt1 + pt2 * pt2;
-    if (m2 > bt * bt) {   // Coulomb disc (Eq. 6)
-        const float s = bt * rsqrtf(m2);
-        pt1 *= s;
-        pt2 *= s;
-    }
-    u.pt1 = pt1;
-    u.pt2 = pt2;
-    // rolling and twisting: ball |p_r| <= mu_r r_eff p_n (Eq. 7)
-    const float3 pr0 = make_float3(l0.w, l1.x, l1.y);
-    float3 pr = pr0 - r1.w * ((wa - wb) + sig_t * pr0);
-    const float br = mur * u.pn;
-    const float q2 = dot(pr, pr);
-    if (q2 > br * br) pr = (br * rsqrtf(q2)) * pr;
-    u.pr = pr;
-    return u;
-}
-
-// A load-driven group's contact at sweep it: the group's iterate instead of
-// the primitive's prescribed velocity, and the contact's impulse added to the
-// group's sum for iterate it + 1 (k_group_contacts).
-static __device__ __forceinline__ Upd geom_update_group(const SimParams& P, const DevBuf& B, const float4* r,
-                                                        float4 l0, float2 l1, float3 vi, float3 wi, int q, int it) {
-    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
-    const float3 vgp = group_velocity(P, B, q, it) + cross(f3(r4), f3(r5));
-    const Upd u = contact_update<true>(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - vgp, wi, f3(r4), P.eps_reg,
-                                       r3.w, r4.w);
-    const float3 n = f3(r0);
-    group_add(B, q, it + 1, (-1.0f) * (u.pn * n + u.pt1 * u.t1 + u.pt2 * u.t2));
-    return u;
-}
-
-// Update of sphere-geometry contact k at sweep it from the body's iterate (vi, wi).
-// A group's contact was updated by k_group_contacts: its new impulse is read.
-static __device__ __forceinline__ Upd geom_update(const SimParams& P, const DevBuf& B, const float4* r, int k,
-                                                  int src, int it, float3 vi, float3 wi, bool& done) {
-    const float4 r0 = r[0];
-    done = __float_as_int(r[5].w) >= 0;
-    Upd u;
-    if (done) {
-        const int dst = src ^ 1;
-        const float4 a = B.glamA[dst][k];
-        const float2 b = B.glamB[dst][k];
-        tangent_basis(f3(r0), u.t1, u.t2);
-        u.pn = a.x; u.pt1 = a.y; u.pt2 = a.z; u.pr = make_float3(a.w, b.x, b.y);
-        return u;
-    }
-    const float4 r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
-    const float4 l0 = B.glamA[src][k];
-    const float2 l1 = B.glamB[src][k];
-    return contact_update(r0, r1, r2.x, 0.0f, r2.y, r2.z, l0, l1, vi - f3(r3), wi, f3(r4), P.eps_reg);
-}
-
-static __device__ __forceinline__ void write_world(float4* W, size_t c, float3 n, const Upd& u) {
-    const float3 pt = u.pt1 * u.t1 + u.pt2 * u.t2;
-    W[2 * c] = make_float4(u.pn, pt.x, pt.y, pt.z);
-    W[2 * c + 1] = make_float4(u.pr.x, u.pr.y, u.pr.z, 0.f);
-}
 
 // ---------------------------------------------------------------------------
 // Body pass (UPDATE = false: v^0 from the warm-start impulses) and projected
@@ -374,7 +265,7 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
                 u.pn = l0.x; u.pt1 = l0.y; u.pt2 = l0.z; u.pr = make_float3(l0.w, l1.x, l1.y);
                 const int q = __float_as_int(r[5].w);
                 if (q >= 0)   // the warm start's impulse on a load-driven group: iterate 0
-                    group_add(B, q, 0, (-1.0f) * (u.pn * n + u.pt1 * u.t1 + u.pt2 * u.t2));
+                    group_add(B, q, 0, (-1.0f) * (u.pn * n + lin2(u.pt1, u.t1, u.pt2, u.t2)));
             }
             if (last && !done) write_world(B.glamW[p], k, n, u);
             add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
@@ -848,7 +739,7 @@ static void sweep_launch(const SimParams& P, const DevBuf& B, int parity, int it
 
 static void sweep_dispatch(const SimParams& P, const DevBuf& B, int parity, int it, int nact, bool update,
                            cudaStream_t s) {
-    switch (P.lanes > 0 ? P.lanes : 2) {
+    switch (P.lanes > 0 && P.lanes <= 8 ? P.lanes : 2) {
         case 1: sweep_launch<1>(P, B, parity, it, nact, update, s); break;
         case 2: sweep_launch<2>(P, B, parity, it, nact, update, s); break;
         case 8: sweep_launch<8>(P, B, parity, it, nact, update, s); break;
@@ -864,7 +755,7 @@ int launch_v0(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
 }
 
 int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int nact, cudaStream_t s) {
-    if (P.lanes > 0) {   // single-kernel sweep, T threads per body
+    if (P.lanes > 0 && P.lanes <= 8) {   // single-kernel sweep, T threads per body
         const int kg = launch_group_contacts(P, B, parity, it, s);
         sweep_dispatch(P, B, parity, it, nact, true, s);
         return 1 + kg;

@@ -4,8 +4,8 @@ against the exact contact predicate on a sample).
 
 - refined bed, 201,686 spheres squeezed to the settled contact density: one step
   against one oracle step (contact set bit-exact, impulses and velocities within
-  1e-5), two-pass sweep (the autotuner's choice for this bed) and one kernel
-  with 2 threads per particle;
+  1e-5), two-pass sweep, one kernel with 2 threads per particle, and the
+  resident sweep (one cooperative kernel per step);
 - triaxial cell, 50,000 spheres: one step against the oracle;
 - fine bed, ~4 M spheres: every contact of 20,000 sampled particles against the
   exact FP64 predicate (KD-tree candidates, then the predicate on the double
@@ -46,7 +46,7 @@ def one_step_parity(x, r, geoms, p, lanes):
     return len(a)
 
 
-@pytest.mark.parametrize("lanes", [0, 2])
+@pytest.mark.parametrize("lanes", [0, 2, 16])
 def test_refined_bed_full_size_one_step(lanes):
     bed = beds.refined_sinkage_bed()
     x = squeezed(bed)

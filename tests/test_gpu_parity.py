@@ -125,10 +125,11 @@ def test_settling_trajectory_200_steps():
     g.close()
 
 
-@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8])
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8, 16])
 def test_dense_trajectory_200_steps(lanes):
     """A compressed cloud in a box under gravity expands and collides for 200
-    steps with warm starts; every sweep variant (threads per particle)."""
+    steps with warm starts; every sweep layout (two-pass, threads per particle,
+    resident)."""
     x, r, geoms, p = cloud_case(1000, 12, n_it=50)
     x0 = x.copy()
     g = make_gpu(x, r, p, geoms, lanes=lanes)

@@ -38,7 +38,8 @@ class _Params(C.Structure):
                 ("mu_t", C.c_double), ("mu_r", C.c_double), ("e_H", C.c_double),
                 ("damp_steps", C.c_double), ("dt", C.c_double), ("n_it", C.c_int32),
                 ("gravity", C.c_double * 3), ("kn_scale", C.c_double),
-                ("eps_reg", C.c_double), ("delta_floor", C.c_double), ("solver", C.c_int32)]
+                ("eps_reg", C.c_double), ("delta_floor", C.c_double), ("solver", C.c_int32),
+                ("e_imp", C.c_double), ("v_imp", C.c_double)]
 
 
 class _Geom(C.Structure):
@@ -64,6 +65,8 @@ class OracleParams:
     eps_reg: float = 1e-6
     delta_floor: float = 1e-8
     solver: int = 0              # 0 Jacobi with mass splitting, 1 coloured projected Gauss-Seidel
+    restitution: float = 0.0     # Newton impact law: restitution coefficient (Sec. 2.2)
+    impact_speed: float = 0.0    # impact threshold [m/s]; 0 = no impact stage
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -72,6 +75,8 @@ class OracleParams:
             setattr(p, k, float(getattr(self, k)))
         p.n_it = int(self.n_it)
         p.solver = int(self.solver)
+        p.e_imp = float(self.restitution)
+        p.v_imp = float(self.impact_speed)
         p.gravity = (C.c_double * 3)(*[float(v) for v in self.gravity])
         return p
 
@@ -136,6 +141,8 @@ def load():
         lib.orc_threads.restype = C.c_int
         lib.orc_colours.restype = C.c_int32
         lib.orc_colours.argtypes = [vp]
+        lib.orc_impacts.restype = C.c_int64
+        lib.orc_impacts.argtypes = [vp]
         lib.orc_step.restype = C.c_int
         lib.orc_set_load.restype = C.c_int
         lib.orc_set_load.argtypes = [vp, C.c_int32, i32, C.c_double, d, C.c_int32]
@@ -205,6 +212,10 @@ class Oracle:
     def colours(self):
         """Colours of the last PGS step (0 for Jacobi)."""
         return int(self.lib.orc_colours(self.h))
+
+    def impacts(self):
+        """Impacting contacts of the last step (0: no impact stage ran)."""
+        return int(self.lib.orc_impacts(self.h))
 
     def state(self):
         x = np.zeros((self.n, 3)); v = np.zeros((self.n, 3)); w = np.zeros((self.n, 3))

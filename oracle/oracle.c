@@ -263,6 +263,8 @@ struct orc_sim {
     int64_t nws;
     double* gforce; /* 6 per geometry */
     int32_t ncol;     /* colours of the last PGS step */
+    int64_t nimp;     /* impacting contacts of the last step */
+    double* gimp;     /* 6 per geometry: impact-stage impulse G_b^T p of the last step */
     /* load-driven rigid groups of primitives (orc_set_load) */
     int32_t ngrp;
     int32_t* gbody;   /* per primitive: its group, or -1 (kinematic) */
@@ -313,6 +315,7 @@ orc_sim* orc_create(const orc_params* p, int32_t n, const double* x, const doubl
     s->g = (orc_geom*)calloc(ng ? ng : 1, sizeof(orc_geom));
     if (ng) memcpy(s->g, g, (size_t)ng * sizeof(orc_geom));
     s->gforce = (double*)calloc(6 * (size_t)(ng ? ng : 1), sizeof(double));
+    s->gimp = (double*)calloc(6 * (size_t)(ng ? ng : 1), sizeof(double));
     s->gbody = (int32_t*)malloc((size_t)(ng ? ng : 1) * sizeof(int32_t));
     for (int32_t k = 0; k < ng; ++k) s->gbody[k] = -1;
     return s;
@@ -340,7 +343,7 @@ int orc_set_load(orc_sim* s, int32_t count, const int32_t* geoms, double mass, c
 void orc_destroy(orc_sim* s) {
     if (!s) return;
     free(s->x); free(s->r); free(s->v); free(s->w); free(s->inv_m); free(s->inv_I);
-    free(s->id); free(s->g); free(s->c); free(s->ws); free(s->gforce); free(s->gbody);
+    free(s->id); free(s->g); free(s->c); free(s->ws); free(s->gforce); free(s->gimp); free(s->gbody);
     free(s);
 }
 
@@ -523,6 +526,91 @@ static int cmp_priority(const void* pa, const void* pb) {
     return before(x, y) ? -1 : (before(y, x) ? 1 : 0);
 }
 
+/* Newton impact stage (Sec. 2.2: high-velocity impacts follow Newton's impact
+ * law while every other kinematic constraint is kept).  A contact whose normal
+ * velocity at the start of the step u- = G_n v is below -v_imp is an impact.
+ * When the step has one, normal impulses p >= 0 of every contact are solved
+ * on the velocity level,
+ *     u+ + e_c min(u-, 0) >= 0   complementary to   p >= 0,
+ *     u+ = G_n v+,  v+ = v + M^-1 G_n^T p,
+ * with e_c = e_imp for impacts and 0 for the other contacts (no approach), by
+ * N_it projected Jacobi sweeps with the masses split over each body's contacts
+ * (as the main solve), from p = 0; primitives keep their velocities.  The
+ * post-impact velocities then start the SPOOK step. */
+static void impact_stage(orc_sim* s, const int32_t* cnt, const int64_t* start, const int64_t* inc) {
+    const orc_params* P = &s->p;
+    const int32_t n = s->n;
+    const int64_t nc = s->nc;
+    s->nimp = 0;
+    memset(s->gimp, 0, 6 * (size_t)(s->ng ? s->ng : 1) * sizeof(double));
+    if (!(P->v_imp > 0.0) || nc == 0) return;
+    double* u0 = (double*)malloc((size_t)nc * sizeof(double));
+    double* tgt = (double*)malloc((size_t)nc * sizeof(double));
+    double* Dinv = (double*)malloc((size_t)nc * sizeof(double));
+    double* p = (double*)calloc((size_t)nc, sizeof(double));
+    double* pn = (double*)calloc((size_t)nc, sizeof(double));
+    for (int64_t k = 0; k < nc; ++k) {
+        const contact* c = &s->c[k];
+        double u = dot3(c->Ga[0], &s->v[3 * c->a]) + dot3(&c->Ga[0][3], &s->w[3 * c->a]);
+        if (c->b >= 0) u += dot3(c->Gb[0], &s->v[3 * c->b]) + dot3(&c->Gb[0][3], &s->w[3 * c->b]);
+        else u += c->known[0];
+        u0[k] = u;
+        const int hit = u < -P->v_imp;
+        tgt[k] = hit ? P->e_imp * u : 0.0;
+        s->nimp += hit;
+        /* D = G_n M_split^-1 G_n^T, primitives kinematic */
+        const double ima = cnt[c->a] * s->inv_m[c->a], iIa = cnt[c->a] * s->inv_I[c->a];
+        double D = 0.0;
+        for (int q = 0; q < 3; ++q) D += c->Ga[0][q] * c->Ga[0][q] * ima + c->Ga[0][3 + q] * c->Ga[0][3 + q] * iIa;
+        if (c->b >= 0) {
+            const double imb = cnt[c->b] * s->inv_m[c->b], iIb = cnt[c->b] * s->inv_I[c->b];
+            for (int q = 0; q < 3; ++q)
+                D += c->Gb[0][q] * c->Gb[0][q] * imb + c->Gb[0][3 + q] * c->Gb[0][3 + q] * iIb;
+        }
+        Dinv[k] = 1.0 / D;
+    }
+    if (s->nimp == 0) {
+        free(u0); free(tgt); free(Dinv); free(p); free(pn);
+        return;
+    }
+    double* v0 = (double*)malloc(3 * (size_t)n * sizeof(double));
+    double* w0 = (double*)malloc(3 * (size_t)n * sizeof(double));
+    memcpy(v0, s->v, 3 * (size_t)n * sizeof(double));
+    memcpy(w0, s->w, 3 * (size_t)n * sizeof(double));
+    for (int32_t it = 0; it < P->n_it; ++it) {
+        /* every contact from the bodies' current iterate */
+        for (int64_t k = 0; k < nc; ++k) {
+            const contact* c = &s->c[k];
+            double u = dot3(c->Ga[0], &s->v[3 * c->a]) + dot3(&c->Ga[0][3], &s->w[3 * c->a]);
+            if (c->b >= 0) u += dot3(c->Gb[0], &s->v[3 * c->b]) + dot3(&c->Gb[0][3], &s->w[3 * c->b]);
+            else u += c->known[0];
+            const double q = p[k] - Dinv[k] * (u + tgt[k]);
+            pn[k] = q > 0.0 ? q : 0.0;
+        }
+        memcpy(p, pn, (size_t)nc * sizeof(double));
+        /* every body: v+ = v + M^-1 sum_c G_n^T p_c, in contact order */
+        for (int32_t i = 0; i < n; ++i) {
+            double acc[6] = {0, 0, 0, 0, 0, 0};
+            for (int64_t e = start[i]; e < start[i + 1]; ++e) {
+                const contact* c = &s->c[inc[e] / 2];
+                const double* row = (inc[e] & 1) ? c->Gb[0] : c->Ga[0];
+                for (int q = 0; q < 6; ++q) acc[q] += row[q] * p[inc[e] / 2];
+            }
+            for (int q = 0; q < 3; ++q) {
+                s->v[3 * i + q] = v0[3 * i + q] + s->inv_m[i] * acc[q];
+                s->w[3 * i + q] = w0[3 * i + q] + s->inv_I[i] * acc[3 + q];
+            }
+        }
+    }
+    /* the impulse the primitives received */
+    for (int64_t k = 0; k < nc; ++k) {
+        const contact* c = &s->c[k];
+        if (c->b >= 0) continue;
+        for (int q = 0; q < 6; ++q) s->gimp[6 * (-c->b - 1) + q] += c->Gb[0][q] * p[k];
+    }
+    free(u0); free(tgt); free(Dinv); free(p); free(pn); free(v0); free(w0);
+}
+
 static void step_once(orc_sim* s) {
     const orc_params* P = &s->p;
     const double h = P->dt;
@@ -623,12 +711,9 @@ static void step_once(orc_sim* s) {
         const double J = P->e_H * pow(dfl, P->e_H - 1.0);
         const double gap = -pow(c->delta, P->e_H);
         const double Sig_scaled = 4.0 * eps_n * Ups / (h * h);
-        /* normal velocity at the start of the step, G_n v_i */
-        double Gv = dot3(c->Ga[0], &s->v[3 * a]) + dot3(&c->Ga[0][3], &s->w[3 * a]);
-        if (c->b >= 0) Gv += dot3(c->Gb[0], &s->v[3 * c->b]) + dot3(&c->Gb[0][3], &s->w[3 * c->b]);
-        else Gv += c->known[0];
         c->sig[0] = Sig_scaled / (J * J);
-        c->rhs[0] = (-(4.0 / h) * Ups * gap) / J + Ups * Gv;
+        /* the gap part of the right side; + Ups G_n v after the impact stage */
+        c->rhs[0] = (-(4.0 / h) * Ups * gap) / J;
         for (int q = 1; q < 6; ++q) { c->sig[q] = P->eps_reg * c->sig[0]; c->rhs[q] = 0.0; }
         c->mu_t = mu_t;
         c->mu_r_reff = mu_r * reff;
@@ -688,6 +773,18 @@ static void step_once(orc_sim* s) {
         int a = s->c[k].a, b = s->c[k].b;
         inc[start[a] + fill[a]++] = 2 * k;          /* side a */
         if (b >= 0) inc[start[b] + fill[b]++] = 2 * k + 1; /* side b */
+    }
+
+    /* 2b. Newton impact stage, then the velocity part of the right side:
+     * b_n = -(4/dt) Ups g / J + Ups G_n v with v the (post-impact) velocity at
+     * the start of the step */
+    impact_stage(s, cnt, start, inc);
+    for (int64_t k = 0; k < s->nc; ++k) {
+        contact* c = &s->c[k];
+        double Gv = dot3(c->Ga[0], &s->v[3 * c->a]) + dot3(&c->Ga[0][3], &s->w[3 * c->a]);
+        if (c->b >= 0) Gv += dot3(c->Gb[0], &s->v[3 * c->b]) + dot3(&c->Gb[0][3], &s->w[3 * c->b]);
+        else Gv += c->known[0];
+        c->rhs[0] = c->rhs[0] + Ups * Gv;
     }
 
     /* free velocity v* = v + dt M^-1 f_ext (gravity only) */
@@ -835,7 +932,8 @@ static void step_once(orc_sim* s) {
         if (c->b >= 0) continue;
         add_GT(c->Gb, c->lam, &s->gforce[6 * (-c->b - 1)]);
     }
-    for (int32_t gi = 0; gi < 6 * s->ng; ++gi) s->gforce[gi] /= h;
+    /* the impact stage's impulse on the geometry belongs to the same step */
+    for (int32_t gi = 0; gi < 6 * s->ng; ++gi) s->gforce[gi] = (s->gforce[gi] + s->gimp[gi]) / h;
 
     /* kinematic geometry: translate with v, rotate with w (Rodrigues) */
     for (int32_t gi = 0; gi < s->ng; ++gi) {
@@ -873,6 +971,7 @@ static void step_once(orc_sim* s) {
 }
 
 int32_t orc_colours(const orc_sim* s) { return s->ncol; }
+int64_t orc_impacts(const orc_sim* s) { return s->nimp; }
 
 int orc_step(orc_sim* s, int32_t nsteps) {
     if (s->p.solver == ORC_PGS && s->ngrp > 0) return -1;

@@ -49,6 +49,9 @@ typedef struct orc_params {
     double delta_floor;  /* floor on the overlap inside the Hertz Jacobian factor [m] */
     int32_t solver;      /* ORC_JACOBI (Jacobi with mass splitting) or ORC_PGS (coloured
                             projected Gauss-Seidel, the paper's PGS ordered by contact colours) */
+    double e_imp;        /* Newton restitution coefficient of the impact stage (Sec. 2.2) */
+    double v_imp;        /* impact threshold: contacts approaching faster than this [m/s] are
+                            impacts; 0 = no impact stage */
 } orc_params;
 
 enum { ORC_JACOBI = 0, ORC_PGS = 1 };
@@ -94,6 +97,8 @@ int orc_set_load(orc_sim* s, int32_t count, const int32_t* geoms, double mass, c
 int orc_step(orc_sim* s, int32_t nsteps);
 /* Colours used by the last step's PGS sweeps (0 for Jacobi). */
 int32_t orc_colours(const orc_sim* s);
+/* Impacting contacts of the last step (0: no impact stage ran). */
+int64_t orc_impacts(const orc_sim* s);
 void orc_get_state(const orc_sim* s, double* x, double* v, double* w);
 void orc_set_state(orc_sim* s, const double* x, const double* v, const double* w);
 void orc_set_geom_velocity(orc_sim* s, int32_t g, const double v[3], const double w[3]);

@@ -109,6 +109,16 @@ typedef struct dem_bed_desc {
                                    colour by colour with the bodies updated in between, unsplit
                                    masses.  PGS runs outside CUDA graphs (a study mode), needs the
                                    same n_it in every bed, no load-driven groups, no adjoint. */
+    float restitution;          /* Newton impact law (Sec. 2.2): restitution coefficient e in
+                                   [0, 1] of impacting contacts */
+    float impact_speed;         /* impact threshold [m/s]; 0 = no impact stage (default).  When a
+                                   bed has a contact whose normal velocity at the start of the step
+                                   is below -impact_speed, a velocity-level stage before the SPOOK
+                                   solve gives every contact of that bed a normal impulse p >= 0
+                                   with u+ >= -e u- for the impacts and u+ >= 0 for the others
+                                   (n_it projected Jacobi sweeps, masses split over each body's
+                                   contacts, primitives kinematic).  Its impulse on primitives is
+                                   part of the step's primitive force.  No adjoint. */
 } dem_bed_desc;
 
 typedef struct dem_bed dem_bed;   /* opaque, library-owned */
@@ -128,6 +138,7 @@ typedef struct dem_info {
     int32_t resort_every;       /* current Morton re-sort period */
     int32_t solver;             /* current solver (see dem_bed_desc.solver) */
     int32_t colours;            /* colours of the last PGS step, 0 for Jacobi */
+    int64_t impacts;            /* impacting contacts of the last step (impact stage) */
 } dem_info;
 
 /* Create a bed from particles, materials and geometry.
@@ -140,7 +151,8 @@ dem_status dem_create_bed(const dem_bed_desc* desc, void* stream, dem_bed** out)
  * (Sec. 3.3, Table 2), fill the GPU together where one alone would not.
  * descs[k] describes bed k exactly as for dem_create_bed; the solver and
  * material settings (dt, e_H, damp_steps, E, nu, mu_t, mu_r, gravity, kn_scale,
- * eps_reg, delta_floor) must be equal across beds, n_it (Eq. 8) may differ.
+ * eps_reg, delta_floor, restitution, impact_speed) must be equal across beds,
+ * n_it (Eq. 8) may differ.
  * Particles of bed k get the stable ids after those of beds 0..k-1, and its
  * primitives the indices after theirs (all dem_read_* calls use these global
  * numbers).  Beds never interact, even where they overlap in space.  Allocator,

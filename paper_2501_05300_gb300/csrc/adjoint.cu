@@ -924,6 +924,7 @@ static dem_status check_supported(dem_bed* b) {
     const SimParams& P = b->P;
     if (!P.nit_uniform) return dem_fail(DEM_ERR_ARG, "the adjoint needs the same n_it in every bed");
     if (P.solver) return dem_fail(DEM_ERR_ARG, "the adjoint reverses the Jacobi solver only");
+    if (P.v_imp > 0.f) return dem_fail(DEM_ERR_ARG, "the adjoint does not reverse the impact stage");
     std::vector<GeomDev> hg(std::max(P.ng, 1));
     if (P.ng > 0) {
         // ordered after pending velocity changes on the bed's stream

@@ -170,7 +170,8 @@ static bool same_settings(const dem_bed_desc& a, const dem_bed_desc& b) {
     return a.E == b.E && a.nu == b.nu && a.mu_t == b.mu_t && a.mu_r == b.mu_r && a.e_H == b.e_H &&
            a.damp_steps == b.damp_steps && a.dt == b.dt && a.gravity[0] == b.gravity[0] &&
            a.gravity[1] == b.gravity[1] && a.gravity[2] == b.gravity[2] && a.kn_scale == b.kn_scale &&
-           a.eps_reg == b.eps_reg && a.delta_floor == b.delta_floor;
+           a.eps_reg == b.eps_reg && a.delta_floor == b.delta_floor && a.restitution == b.restitution &&
+           a.impact_speed == b.impact_speed;
 }
 
 static dem_status check_desc(const dem_bed_desc* d, int k) {
@@ -446,6 +447,14 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
         release(b);
         return fail(DEM_ERR_ARG, "solver = %d is not 0 (Jacobi) or 1 (coloured Gauss-Seidel)", d->solver);
     }
+    if (!(d->restitution >= 0.f && d->restitution <= 1.f) || !(d->impact_speed >= 0.f) ||
+        !std::isfinite(d->impact_speed)) {
+        release(b);
+        return fail(DEM_ERR_ARG, "need 0 <= restitution <= 1 and a finite impact_speed >= 0");
+    }
+    P.e_imp = d->restitution;
+    P.v_imp = d->impact_speed;
+    P.n_beds = nbeds;
     for (int k = 1; k < nbeds && P.solver; ++k)
         if (descs[k].n_it != descs[0].n_it) {
             release(b);
@@ -647,6 +656,7 @@ static int body_pre(dem_bed* b, int p) {
                       B.geo_start[p], P.n, B.scan_tmp, s);
     k += launch_contacts_build(P, B, p, s);
     k += launch_inc_sort(P, B, s);
+    if (P.v_imp > 0.f && b->imp.row) k += launch_impact(P, B, b->imp, p, s);
     k += launch_setup(P, B, p, s);
     k += launch_v0(P, B, p, s);
     return k;
@@ -670,6 +680,27 @@ static int body_resort(dem_bed* b, int) { return launch_resort(b->P, b->B, b->st
 
 static dem_status build_graphs(dem_bed* b) {
     dem_status st;
+    if (b->P.v_imp > 0.f && !b->imp.row) {
+        // once: the impact stage's rows and iterates at contact capacity
+        ImpBuf I{};
+        const size_t C = b->P.max_contacts, G = b->P.max_geo;
+        auto al = [&](void** q, size_t bytes) { if (st == DEM_OK) st = dalloc(b, q, bytes); };
+        st = DEM_OK;
+        al((void**)&I.row, C * sizeof(float4));
+        al((void**)&I.tgt, C * sizeof(float));
+        al((void**)&I.p[0], C * sizeof(float));
+        al((void**)&I.p[1], C * sizeof(float));
+        al((void**)&I.grow, G * sizeof(float4));
+        al((void**)&I.glev, G * sizeof(float4));
+        al((void**)&I.gtgt, G * sizeof(float));
+        al((void**)&I.gp[0], G * sizeof(float));
+        al((void**)&I.gp[1], G * sizeof(float));
+        al((void**)&I.bed, std::max(b->nbeds, 1) * sizeof(int));
+        al((void**)&I.count, sizeof(int));
+        if (st != DEM_OK) return st;
+        CK(cudaMemsetAsync(I.count, 0, sizeof(int), b->stream));
+        b->imp = I;
+    }
     int blocks = 0;
     if (b->P.lanes == DEM_LAYOUT_RESIDENT && resident_ok(b->P, &blocks) && !b->res.prog) {
         // once: the blocks' progress counters
@@ -1093,6 +1124,12 @@ extern "C" dem_status dem_get_info(dem_bed* b, dem_info* out) {
     out->resort_every = b->resort_every;
     out->solver = b->P.solver;
     out->colours = b->P.solver ? b->pgs_colours : 0;
+    if (b->imp.count && b->steps > 0) {
+        int m = 0;
+        CK(cudaMemcpyAsync(&m, b->imp.count, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        out->impacts = b->P.v_imp > 0.f ? m : 0;
+    }
     if (b->steps > 0 && b->P.n > 0) {
         const int p = (int)((b->steps - 1) & 1);
         int a = 0, g = 0;
@@ -1151,6 +1188,9 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
         return fail(DEM_ERR_ARG, "bad lanes");
     const int solver = d->solver >= 0 ? d->solver : b->P.solver;
     if (solver != 0 && solver != 1) return fail(DEM_ERR_ARG, "bad solver");
+    const float e_imp = d->restitution >= 0.f ? d->restitution : b->P.e_imp;
+    const float v_imp = d->impact_speed >= 0.f ? d->impact_speed : b->P.v_imp;
+    if (!(e_imp <= 1.f) || !std::isfinite(v_imp)) return fail(DEM_ERR_ARG, "bad restitution or impact_speed");
     if (solver && b->P.n_groups > 0)
         return fail(DEM_ERR_ARG, "the Gauss-Seidel solver does not take load-driven groups");
     CK(cudaSetDevice(b->dev));
@@ -1178,6 +1218,8 @@ extern "C" dem_status dem_set_params(dem_bed* b, const dem_bed_desc* d) {
     P.gx = d->gravity[0]; P.gy = d->gravity[1]; P.gz = d->gravity[2];
     P.lanes = lanes;
     P.solver = solver;
+    P.e_imp = e_imp;
+    P.v_imp = v_imp;
     CK(cudaMemcpyAsync(b->B.lv, b->levels.data(), b->levels.size() * sizeof(LevelGrid), cudaMemcpyHostToDevice,
                        b->stream));
     CK(cudaStreamSynchronize(b->stream));

@@ -48,6 +48,8 @@ struct dem_bed {
     int pgs_colours = 0;        // colours of the last PGS step
     // resident-sweep buffers (layout DEM_LAYOUT_RESIDENT), created on first use
     ResBuf res{};
+    // Newton impact stage buffers, created when the stage is first enabled
+    ImpBuf imp{};
 };
 
 // error reporting through dem_last_error(); printf-style message

@@ -98,6 +98,9 @@ struct SimParams {
     int nit_uniform;    // 1 when every bed takes n_it sweeps
     int n_groups;       // load-driven groups
     int solver;         // 0 projected Jacobi (mass splitting), 1 coloured projected Gauss-Seidel
+    float e_imp;        // Newton impact stage: restitution coefficient
+    float v_imp;        // impact threshold [m/s]; 0: no impact stage
+    int n_beds;
 };
 
 // Device pointers of one bed.  The two warm-start generations (parity of the
@@ -217,6 +220,21 @@ int launch_pgs_round(const SimParams& P, const DevBuf& B, const PgsBuf& S, int p
 int launch_pgs_bucket(const PgsBuf& S, int total, bool fill, cudaStream_t s);
 int launch_pgs_colour(const SimParams& P, const DevBuf& B, const PgsBuf& S, int parity, int nc, int first,
                       int count, bool last, cudaStream_t s);
+
+// Newton impact stage (Sec. 2.2), run before the contact rows when the
+// threshold is set; its buffers are allocated when it is first enabled.
+struct ImpBuf {
+    float4* row;        // [C] (n, 1 / D) of each sphere-sphere contact
+    float* tgt;         // [C] e u- for impacts, 0 for the other contacts
+    float* p[2];        // [C] normal impulse iterates
+    float4* grow;       // [G] (n, 1 / D) of each sphere-geometry contact
+    float4* glev;       // [G] (lever from the primitive's centre, n . velocity of its point)
+    float* gtgt;        // [G]
+    float* gp[2];       // [G]
+    int* bed;           // [n_beds] 1 when the bed has an impact this step
+    int* count;         // [1] impacting contacts this step
+};
+int launch_impact(const SimParams& P, const DevBuf& B, const ImpBuf& I, int parity, cudaStream_t s);
 
 // Resident sweep (layout DEM_LAYOUT_RESIDENT): all sweeps of a step in one
 // cooperative kernel, one block per SM, each block keeping a contiguous range

@@ -57,7 +57,8 @@ class dem_bed_desc(C.Structure):
                 ("geom", C.POINTER(dem_geom)), ("contact_capacity", C.c_int64),
                 ("resort_every", C.c_int32), ("level_ratio", C.c_float), ("lanes", C.c_int32),
                 ("alloc", ALLOC_FN),
-                ("free_fn", FREE_FN), ("alloc_ctx", C.c_void_p), ("solver", C.c_int32)]
+                ("free_fn", FREE_FN), ("alloc_ctx", C.c_void_p), ("solver", C.c_int32),
+                ("restitution", C.c_float), ("impact_speed", C.c_float)]
 
 
 class dem_info(C.Structure):
@@ -65,7 +66,8 @@ class dem_info(C.Structure):
                 ("contacts", C.c_int64), ("geom_contacts", C.c_int64), ("steps", C.c_int64),
                 ("contact_capacity", C.c_int64), ("kernels_per_step", C.c_int32),
                 ("kernels_per_resort", C.c_int32), ("n_beds", C.c_int32), ("lanes", C.c_int32),
-                ("resort_every", C.c_int32), ("solver", C.c_int32), ("colours", C.c_int32)]
+                ("resort_every", C.c_int32), ("solver", C.c_int32), ("colours", C.c_int32),
+                ("impacts", C.c_int64)]
 
 
 _lib = None
@@ -192,7 +194,8 @@ class _TorchAllocator:
 def _make_desc(x, r, keep, *, v=None, w=None, geoms=(), rho=2600.0, E=1e9, nu=0.15, mu_t=0.5,
                mu_r=0.02, e_H=1.25, damp_steps=4.5, dt=1e-5, n_it=100, gravity=(0.0, 0.0, -9.81),
                kn_scale=1.0, eps_reg=1e-6, delta_floor=0.0, inv_mass=None, inv_inertia=None,
-               contact_capacity=0, resort_every=0, level_ratio=0.0, lanes=0, solver=0):
+               contact_capacity=0, resort_every=0, level_ratio=0.0, lanes=0, solver=0, restitution=0.0,
+               impact_speed=0.0):
     """A dem_bed_desc for one bed; arrays that must outlive the call go to keep."""
     x = _input(x, np.float64, (-1, 3))
     r = _input(r, np.float32, (-1,))
@@ -223,6 +226,7 @@ def _make_desc(x, r, keep, *, v=None, w=None, geoms=(), rho=2600.0, E=1e9, nu=0.
     d.level_ratio = float(level_ratio)
     d.lanes = int(lanes)
     d.solver = int(solver)
+    d.restitution, d.impact_speed = float(restitution), float(impact_speed)
     return d, n, geoms
 
 
@@ -343,13 +347,14 @@ class Bed:
         return a.value, j.value, s.value
 
     def set_params(self, *, dt, n_it, mu_t, mu_r, damp_steps=4.5, e_H=1.25, gravity=(0.0, 0.0, -9.81),
-                   kn_scale=1.0, eps_reg=1e-6, lanes=0, solver=-1):
+                   kn_scale=1.0, eps_reg=1e-6, lanes=0, solver=-1, restitution=-1.0, impact_speed=-1.0):
         """Change solver and material settings between steps (dem_set_params);
-        solver -1 keeps the current one."""
+        solver, restitution and impact_speed -1 keep the current ones."""
         d = dem_bed_desc()
         d.dt, d.n_it, d.mu_t, d.mu_r, d.damp_steps, d.e_H = dt, int(n_it), mu_t, mu_r, damp_steps, e_H
         d.gravity = (C.c_float * 3)(*map(float, gravity))
         d.kn_scale, d.eps_reg, d.lanes, d.solver = kn_scale, eps_reg, int(lanes), int(solver)
+        d.restitution, d.impact_speed = float(restitution), float(impact_speed)
         _check(self.lib.dem_set_params(self._handle, C.byref(d)))
         self.dt = dt
         self.params = dict(dt=dt, n_it=int(n_it), mu_t=mu_t, mu_r=mu_r, damp_steps=damp_steps, e_H=e_H,

@@ -595,6 +595,51 @@ def run_triaxial(args):
 SOLVER_NITS = (5, 10, 20, 40, 74, 150, 300, 600)
 
 
+IMPACT_E, IMPACT_V = 0.5, 0.05     # restitution and threshold of the impact study (R9 leaves both open)
+
+
+def run_impact(args, steps=1000):
+    """The settling box (2,000 spheres dropped from a loose lattice, 1,000 steps
+    at dt 1e-5 s, N_it 100) without and with the Newton impact stage: step cost,
+    impacts per step and the kinetic energy left after the drop."""
+    import torch
+    from paper_2501_05300_gb300 import dem
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    spec = beds.settling_box()
+    m = spec.material
+    out = {}
+    for name, (e, vi) in (("plain", (0.0, 0.0)), ("impact", (IMPACT_E, IMPACT_V))):
+        bed = dem.Bed(spec.x, spec.r, geoms=spec.geoms, rho=m.rho, mu_t=m.mu_t, mu_r=m.mu_r, n_it=100, dt=DT,
+                      lanes=0, restitution=e, impact_speed=vi)
+        start = bed.save_checkpoint()
+        bed.step(3)
+        bed.restore_checkpoint(start)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bed.step(steps)
+        bed.sync()
+        el = time.perf_counter() - t0
+        _, v, w = bed.read_state()
+        mass = m.rho * 4.0 / 3.0 * np.pi * spec.r.astype(np.float64) ** 3
+        ke = float(0.5 * (mass * (v.astype(np.float64) ** 2).sum(1)).sum())
+        counts = []
+        if vi > 0:                         # impacts per step, on a second pass
+            bed.restore_checkpoint(start)
+            for _ in range(steps // 10):
+                bed.step(10)
+                counts.append(bed.info().impacts)
+        bed.free_checkpoint(start)
+        bed.close()
+        out[name] = dict(ms_per_step=el / steps * 1e3, kinetic_energy_J=ke,
+                         impacts_sampled_every_10_steps=dict(max=max(counts), mean=float(np.mean(counts)))
+                         if counts else None)
+    out["overhead"] = out["impact"]["ms_per_step"] / out["plain"]["ms_per_step"]
+    out["restitution"], out["impact_speed"] = IMPACT_E, IMPACT_V
+    out["particles"] = int(spec.n)
+    return out
+
+
 def run_solvers(args):
     """Jacobi (mass splitting) against coloured projected Gauss-Seidel on the
     settled refined bed: one step from the same warm-started state for each
@@ -706,6 +751,8 @@ def main():
     ap.add_argument("--fine-small", action="store_true", help="with --fine: a quarter of the footprint (~1 M)")
     ap.add_argument("--calibrate", action="store_true",
                     help="gradient-driven calibration of the refined triaxial cell against the fine one")
+    ap.add_argument("--impact", action="store_true",
+                    help="the settling box without and with the Newton impact stage")
     ap.add_argument("--solvers", action="store_true",
                     help="Jacobi against coloured Gauss-Seidel: iterations to tolerance on the refined bed")
     ap.add_argument("--triaxial", action="store_true",
@@ -757,6 +804,14 @@ def main():
                           "config": {"workload": "mean deviatoric stress of a refined triaxial cell (coarse lower "
                                                  "half) matched to the 50k fine cell by Newton steps on mu_t with "
                                                  "adjoint gradients", **r}}))
+        return
+    if args.impact:
+        r = run_impact(args)
+        print(json.dumps({"metric": "impact stage cost (step time with / without)", "value": r["overhead"],
+                          "unit": "x", "higher_is_better": False, "n_gpus": 1, "steps": 1000, "dtype": "f32",
+                          "data": "synthetic",
+                          "config": {"workload": "settling box: 2,000 spheres r~U[5,6] mm dropped from a loose "
+                                                 "lattice in a 0.1 x 0.1 m box, dt 1e-5 s, N_it 100", **r}}))
         return
     if args.solvers:
         r = run_solvers(args)

@@ -96,6 +96,7 @@ static void release(dem_bed* b) {
         for (int k = 0; k < 3; ++k)
             if (b->g[p][k]) cudaGraphExecDestroy(b->g[p][k]);
     if (b->g_resort) cudaGraphExecDestroy(b->g_resort);
+    if (b->side) cudaStreamDestroy(b->side);
     dem_adjoint_release(b);
     for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : b->ev_used) cudaEventDestroy(e);
@@ -611,9 +612,15 @@ static dem_status capture(dem_bed* b, cudaGraphExec_t* exec, int* kernels,
     cudaStream_t s = b->stream;
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    b->capture_err = 0;
     int k = body(b, arg);
     cudaError_t le = cudaGetLastError();
     cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (b->capture_err && e == cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(DEM_ERR_CUDA, "graph construction during capture: %s",
+                    cudaGetErrorString((cudaError_t)b->capture_err));
+    }
     if (le != cudaSuccess) return fail(DEM_ERR_CUDA, "kernel launch during capture: %s", cudaGetErrorString(le));
     if (e != cudaSuccess) return fail(DEM_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(exec, graph, 0);
@@ -656,7 +663,11 @@ static int body_pre(dem_bed* b, int p) {
                       B.geo_start[p], P.n, B.scan_tmp, s);
     k += launch_contacts_build(P, B, p, s);
     k += launch_inc_sort(P, B, s);
-    if (P.v_imp > 0.f && b->imp.row) k += launch_impact(P, B, b->imp, p, s);
+    if (P.v_imp > 0.f && b->imp.row) {
+        const int ki = launch_impact(P, B, b->imp, p, s, b->side);
+        if (ki < 0) b->capture_err = -ki;
+        else k += ki;
+    }
     k += launch_setup(P, B, p, s);
     k += launch_v0(P, B, p, s);
     return k;
@@ -701,6 +712,7 @@ static dem_status build_graphs(dem_bed* b) {
         CK(cudaMemsetAsync(I.count, 0, sizeof(int), b->stream));
         b->imp = I;
     }
+    if (b->P.v_imp > 0.f && !b->side) CK(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
     int blocks = 0;
     if (b->P.lanes == DEM_LAYOUT_RESIDENT && resident_ok(b->P, &blocks) && !b->res.prog) {
         // once: the blocks' progress counters

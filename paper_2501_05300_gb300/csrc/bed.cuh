@@ -50,6 +50,8 @@ struct dem_bed {
     ResBuf res{};
     // Newton impact stage buffers, created when the stage is first enabled
     ImpBuf imp{};
+    int capture_err = 0;        // CUDA error of a graph call made while capturing (0: none)
+    cudaStream_t side = nullptr;   // captures the bodies of conditional graph nodes
 };
 
 // error reporting through dem_last_error(); printf-style message

@@ -234,7 +234,9 @@ struct ImpBuf {
     int* bed;           // [n_beds] 1 when the bed has an impact this step
     int* count;         // [1] impacting contacts this step
 };
-int launch_impact(const SimParams& P, const DevBuf& B, const ImpBuf& I, int parity, cudaStream_t s);
+// side: an idle stream that captures the sweeps into a conditional node's body
+int launch_impact(const SimParams& P, const DevBuf& B, const ImpBuf& I, int parity, cudaStream_t s,
+                  cudaStream_t side);
 
 // Resident sweep (layout DEM_LAYOUT_RESIDENT): all sweeps of a step in one
 // cooperative kernel, one block per SM, each block keeping a contiguous range

@@ -17,7 +17,9 @@
 // Layout: one thread per body.  A sweep recomputes each contact's impulse at
 // both of its ends from the same inputs (bit-identical) and each end keeps its
 // own share, so one kernel per sweep suffices; beds without an impact return
-// at once.
+// at once.  Inside a CUDA graph the sweeps sit in the body of a conditional
+// (IF) node that the rows' count opens, so a step without any impact costs
+// two small kernels.
 #include <algorithm>
 
 #include "dem_internal.cuh"
@@ -146,14 +148,59 @@ __global__ void __launch_bounds__(IM_T) k_impact_final(SimParams P, DevBuf B, Im
     }
 }
 
+// opens the conditional body when the step has an impact (one thread: the
+// condition must not be set concurrently)
+__global__ void k_impact_open(ImpBuf I, cudaGraphConditionalHandle h) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, *I.count > 0 ? 1u : 0u);
+}
+
 static inline int nblk(int n, int t) { return n > 0 ? (n + t - 1) / t : 1; }
 
-int launch_impact(const SimParams& P, const DevBuf& B, const ImpBuf& I, int parity, cudaStream_t s) {
-    cudaMemsetAsync(I.bed, 0, std::max(P.n_beds, 1) * sizeof(int), s);
-    cudaMemsetAsync(I.count, 0, sizeof(int), s);
+static void impact_sweeps(const SimParams& P, const DevBuf& B, const ImpBuf& I, int parity, cudaStream_t s) {
     const int blocks = nblk(P.n, IM_T);
-    k_impact_rows<<<blocks, IM_T, 0, s>>>(P, B, I, parity);
     for (int it = 0; it < P.n_it; ++it) k_impact_sweep<<<blocks, IM_T, 0, s>>>(P, B, I, parity, it);
     k_impact_final<<<blocks, IM_T, 0, s>>>(P, B, I, parity);
-    return 2 + P.n_it;
+}
+
+// Returns the kernels launched unconditionally; a negative value is a CUDA
+// error code of the graph calls (as -(int)error).
+int launch_impact(const SimParams& P, const DevBuf& B, const ImpBuf& I, int parity, cudaStream_t s,
+                  cudaStream_t side) {
+    cudaMemsetAsync(I.bed, 0, std::max(P.n_beds, 1) * sizeof(int), s);
+    cudaMemsetAsync(I.count, 0, sizeof(int), s);
+    k_impact_rows<<<nblk(P.n, IM_T), IM_T, 0, s>>>(P, B, I, parity);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g);
+    if (e != cudaSuccess) return -(int)e;
+    if (cs != cudaStreamCaptureStatusActive) {   // eager: every sweep, beds without an impact return at once
+        impact_sweeps(P, B, I, parity, s);
+        return 3 + P.n_it;
+    }
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return -(int)e;
+    k_impact_open<<<1, 32, 0, s>>>(I, h);
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd)) != cudaSuccess) return -(int)e;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, edges, nd, &cp)) != cudaSuccess) return -(int)e;
+    // the body: the sweeps and the final update, captured on the side stream
+    if ((e = cudaStreamBeginCaptureToGraph(side, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return -(int)e;
+    impact_sweeps(P, B, I, parity, side);
+    cudaGraph_t body = nullptr;
+    if ((e = cudaStreamEndCapture(side, &body)) != cudaSuccess) return -(int)e;
+    // the rest of the step waits for the conditional node
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return -(int)e;
+    return 4;
 }

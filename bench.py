@@ -595,6 +595,127 @@ def run_triaxial(args):
 SOLVER_NITS = (5, 10, 20, 40, 74, 150, 300, 600)
 
 
+PROTO = dict(F_N=2550.0, t1=2.5, load_ramp=0.25, ramp=0.1, t2=3.0, t_end=5.4, v_pull=0.1, dt=1e-4, mass=10.0)
+PROTO_BEDS = (("reference: uniform d 8.5 mm", {}),
+              ("low gamma 0.023: 8.5 -> 15 mm", dict(d_max=15e-3, growth=1.1, eta=4.0)),
+              ("medium gamma 0.100: 8.5 -> 22.5 mm", dict(d_max=22.5e-3, growth=1.25, eta=2.0)),
+              ("high gamma 0.500: 8.5 -> 30 mm", dict(d_max=30e-3, growth=2.0, eta=1.0)))
+
+
+def protocol_one(dem, label, cfg, scale, settle_steps):
+    """One bed through the pressure-sinkage and shear-displacement test of
+    Sec. 3.3 with every phase time multiplied by `scale`: phase I the plate
+    under F_N = 2550 N (vertical dynamics, weight included), the load raised
+    linearly over the first `load_ramp` of phase I; from t1 the pull speed
+    ramps 0 -> 0.1 m/s over `ramp`, then holds to t_end.  Samples the plate's
+    sinkage and the pull force F_T = -F_x on it every millisecond."""
+    import torch
+    P = PROTO
+    spec = beds.shear_slice(**cfg)
+    m = spec.material
+    d_min = 8.5e-3
+    bed = dem.Bed(spec.x, spec.r, geoms=spec.geoms, rho=m.rho, mu_t=0.1, mu_r=0.01, n_it=100, dt=2e-4, lanes=0)
+    bed.step(settle_steps)
+    x, _, _ = bed.read_state()
+    h = float((x[:, 2] + spec.r).max())
+    if cfg:
+        _, zmax = beds.shear_slice_layers(d_min, cfg["d_max"], cfg["growth"], cfg["eta"])
+        n_d = rules.network_length_refined(cfg["eta"], d_min, cfg["d_max"], cfg["growth"], h, zmax)
+    else:
+        n_d = rules.network_length_uniform(h, d_min)
+    nit = rules.n_iterations(n_d, 0.02)
+    dt = P["dt"]
+    bed.set_params(dt=dt, n_it=nit, mu_t=m.mu_t, mu_r=m.mu_r, lanes=-1)
+    bed.autotune(2)
+    bed.step(20)
+    # grouser tips 1 mm above the highest particle top under the plate
+    x, _, _ = bed.read_state()
+    pc = spec.geoms[spec.plate]
+    under = (np.abs(x[:, 0] - pc.c[0]) <= pc.he[0]) & (np.abs(x[:, 1] - pc.c[1]) <= pc.he[1])
+    top = float((x[under, 2] + spec.r[under]).max())
+    parts = list(spec.plate_parts)
+    tips = min(bed.read_geom(g).c[2] - spec.geoms[g].he[2] for g in parts[1:])
+    drop = (tips - (top + 1e-3)) / dt
+    for g in parts:
+        bed.apply_plate_velocity(g, (0.0, 0.0, -drop))
+    bed.step(1)
+    for g in parts:
+        bed.apply_plate_velocity(g, (0.0, 0.0, 0.0))
+    bed.apply_plate_load(parts, P["mass"], (0.0, 0.0, 0.0), dof=4)
+    z_surface = top
+    tip_off = bed.read_geom(parts[0]).c[2] - min(bed.read_geom(g).c[2] - spec.geoms[g].he[2] for g in parts[1:])
+    t1, ramp, t_end = P["t1"] * scale, P["ramp"] * scale, P["t_end"] * scale
+    t_load = P["load_ramp"] * scale
+    f_now = 0.0
+    n_steps = int(round(t_end / dt))
+    every = max(1, int(round(1e-3 / dt)))
+    samples = []
+    vx_now = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = 0
+    while k < n_steps:
+        t = k * dt
+        vx = 0.0 if t < t1 else min(1.0, (t - t1) / ramp) * P["v_pull"]
+        if vx != vx_now:
+            bed.apply_plate_velocity(parts[0], (vx, 0.0, 0.0))
+            vx_now = vx
+        f = min(1.0, (k + 1) * dt / t_load) * P["F_N"]
+        if f != f_now:
+            bed.set_plate_load(parts[0], (0.0, 0.0, -f))
+            f_now = f
+        ramping = t1 <= t < t1 + ramp or k * dt < t_load
+        n = 1 if ramping else min(every - k % every, n_steps - k)
+        bed.step(n)
+        k += n
+        if k % every == 0 or k == n_steps:
+            fx = sum(bed.read_forces(g)[0][0] for g in parts)
+            zc = bed.read_geom(parts[0]).c[2]
+            samples.append((k * dt, z_surface - (zc - tip_off), -fx))
+    bed.sync()
+    wall = time.perf_counter() - t0
+    info = bed.info()
+    bed.close()
+    a = np.array(samples)
+    t, sink, ft = a[:, 0], a[:, 1], a[:, 2]
+    tr = ft / P["F_N"]
+    in1 = t <= t1
+    in2 = (t > t1) & (t <= P["t2"] * scale)
+    in23 = t > t1
+    return dict(bed=label, particles=int(spec.n), n_it=nit, sweep_layout=info.lanes, steps=n_steps,
+                ms_per_step=wall / n_steps * 1e3,
+                static_sinkage_m=float(sink[in1][-1]), dynamic_sinkage_m=float(sink[-1]),
+                peak_traction=float(tr[in2].max()), avg_traction=float(tr[in23].mean()),
+                samples=len(samples))
+
+
+def run_protocol(args):
+    """The shear test of Sec. 3.3 (phases I-III) on the 8.5 mm reference slice
+    and three refined slices; the paper's measures (static and dynamic
+    sinkage, peak traction in phase II, average traction in II-III), their
+    normalised errors against the reference (sinkage over the 43 mm grouser
+    depth, traction force over F_N,max = 2550 N) and their mean, the aggregate
+    error."""
+    import torch
+    from paper_2501_05300_gb300 import dem
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    scale = args.protocol_scale
+    runs = [protocol_one(dem, label, cfg, scale, 2 * args.settle) for label, cfg in PROTO_BEDS]
+    ref = runs[0]
+    for r in runs[1:]:
+        e = [(r["static_sinkage_m"] - ref["static_sinkage_m"]) / beds.H_GROUSER,
+             (r["dynamic_sinkage_m"] - ref["dynamic_sinkage_m"]) / beds.H_GROUSER,
+             (r["peak_traction"] - ref["peak_traction"]) * PROTO["F_N"] / PROTO["F_N"],
+             (r["avg_traction"] - ref["avg_traction"]) * PROTO["F_N"] / PROTO["F_N"]]
+        r["normalised_errors"] = dict(static_sinkage=e[0], dynamic_sinkage=e[1], peak_traction=e[2],
+                                      avg_traction=e[3])
+        r["aggregate_error"] = float(np.mean(np.abs(e)))
+        r["particle_reduction"] = ref["particles"] / r["particles"]
+        r["speedup"] = ref["ms_per_step"] / r["ms_per_step"]
+    return dict(time_scale=scale, protocol=PROTO, runs=runs)
+
+
 IMPACT_E, IMPACT_V = 0.5, 0.05     # restitution and threshold of the impact study (R9 leaves both open)
 
 
@@ -751,6 +872,11 @@ def main():
     ap.add_argument("--fine-small", action="store_true", help="with --fine: a quarter of the footprint (~1 M)")
     ap.add_argument("--calibrate", action="store_true",
                     help="gradient-driven calibration of the refined triaxial cell against the fine one")
+    ap.add_argument("--protocol", action="store_true",
+                    help="the pressure-sinkage / shear-displacement test (phases I-III) on the reference and "
+                         "three refined slices")
+    ap.add_argument("--protocol-scale", type=float, default=1.0,
+                    help="with --protocol: multiplies every phase time (1 = the paper's 5.4 s)")
     ap.add_argument("--impact", action="store_true",
                     help="the settling box without and with the Newton impact stage")
     ap.add_argument("--solvers", action="store_true",
@@ -804,6 +930,16 @@ def main():
                           "config": {"workload": "mean deviatoric stress of a refined triaxial cell (coarse lower "
                                                  "half) matched to the 50k fine cell by Newton steps on mu_t with "
                                                  "adjoint gradients", **r}}))
+        return
+    if args.protocol:
+        r = run_protocol(args)
+        med = r["runs"][2]
+        print(json.dumps({"metric": "aggregate normalised error vs the 8.5 mm reference (medium gamma)",
+                          "value": med["aggregate_error"], "unit": "1", "higher_is_better": False, "n_gpus": 1,
+                          "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": "pressure-sinkage and shear-displacement test of a grousered "
+                                                 "plate under 2550 N on a 1.5 x 0.17 x 0.6 m slice (Sec. 3.3), "
+                                                 "phase times x %g, dt 1e-4 s" % r["time_scale"], **r}}))
         return
     if args.impact:
         r = run_impact(args)

@@ -236,6 +236,12 @@ dem_status dem_set_params(dem_bed* bed, const dem_bed_desc* desc);
 dem_status dem_apply_plate_load(dem_bed* bed, const int32_t* geoms, int32_t count, double mass,
                                 const double force[3], int32_t dof);
 
+/* Change the external force [N] of the load-driven group that primitive geom
+ * belongs to, from the next step on (a load applied gradually, as at the start
+ * of the pressure-sinkage test of Sec. 3.3).  Stream-ordered, no
+ * synchronisation.  DEM_ERR_ARG if geom is in no group or force is not finite. */
+dem_status dem_set_plate_load(dem_bed* bed, int32_t geom, const double force[3]);
+
 /* ---- differentiation (reverse mode) -------------------------------------
  * Gradients of J = sum_t sum_g dJ_dF[t][g] . F_t,g, a linear functional of
  * the force on every primitive in every step, with respect to the scale s_k of

@@ -146,6 +146,8 @@ def load():
         lib.orc_step.restype = C.c_int
         lib.orc_set_load.restype = C.c_int
         lib.orc_set_load.argtypes = [vp, C.c_int32, i32, C.c_double, d, C.c_int32]
+        lib.orc_set_load_force.restype = C.c_int
+        lib.orc_set_load_force.argtypes = [vp, C.c_int32, d]
         _lib = lib
     return _lib
 
@@ -254,6 +256,11 @@ class Oracle:
         g = np.ascontiguousarray(geoms, np.int32)
         if self.lib.orc_set_load(self.h, len(g), g, float(mass), np.asarray(force, np.float64), int(dof)) != 0:
             raise ValueError("orc_set_load rejected its arguments")
+
+    def set_load_force(self, g, force):
+        """New external force of the group holding primitive g (orc_set_load_force)."""
+        if self.lib.orc_set_load_force(self.h, int(g), np.asarray(force, np.float64)) != 0:
+            raise ValueError("primitive %d is in no load-driven group" % g)
 
     def set_warmstart(self, key_a, key_b, lam7):
         ka = np.ascontiguousarray(key_a, np.int32); kb = np.ascontiguousarray(key_b, np.int32)

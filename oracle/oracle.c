@@ -340,6 +340,12 @@ int orc_set_load(orc_sim* s, int32_t count, const int32_t* geoms, double mass, c
     return 0;
 }
 
+int orc_set_load_force(orc_sim* s, int32_t g, const double force[3]) {
+    if (g < 0 || g >= s->ng || s->gbody[g] < 0) return -1;
+    for (int a = 0; a < 3; ++a) s->grp[s->gbody[g]].force[a] = force[a];
+    return 0;
+}
+
 void orc_destroy(orc_sim* s) {
     if (!s) return;
     free(s->x); free(s->r); free(s->v); free(s->w); free(s->inv_m); free(s->inv_I);

@@ -93,6 +93,9 @@ void orc_destroy(orc_sim* s);
  * for bad arguments or a primitive already in a group. */
 int orc_set_load(orc_sim* s, int32_t count, const int32_t* geoms, double mass, const double force[3],
                  int32_t dof);
+/* New external force of the group that primitive g belongs to, from the next
+ * step on.  Returns 0, or -1 if g is in no group. */
+int orc_set_load_force(orc_sim* s, int32_t g, const double force[3]);
 /* Returns 0, or -1 (nothing done) for the PGS solver with load-driven groups. */
 int orc_step(orc_sim* s, int32_t nsteps);
 /* Colours used by the last step's PGS sweeps (0 for Jacobi). */

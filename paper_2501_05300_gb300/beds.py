@@ -296,6 +296,52 @@ def fine_shear_bed(lx=1.0, ly=0.5, depth=0.25, seed=2504, phi=0.636, r_nom=2.5e-
                plate=first, plate_parts=tuple(range(first, len(geoms))), box=(lx, ly, depth))
 
 
+SLICE = dict(lx=1.5, ly=0.17, depth=0.6)        # the shear-test container (Sec. 3.3)
+H_GROUSER, L_GROUSER = 0.043, 0.0255             # grouser depth and length at the bottom (Sec. 3.3)
+
+
+def shear_slice(d_min=8.5e-3, d_max=None, growth=1.25, eta=2.0, seed=2507, phi=0.636, plate_x=0.3,
+                t_plate=0.01, n_grousers=3):
+    """The pressure-sinkage / shear-displacement container of Sec. 3.3: a
+    1.5 m long, 0.17 m wide slice of a bed 0.6 m deep, frictionless walls.
+    Uniform particles of diameter d_min (d_max None), or refined: layers from
+    the surface down with d_n = growth d_{n-1} and thickness eta d_n (Sec. 2.1),
+    capped at d_max, which fills the rest (10% size spread in every layer).
+    The plate is 0.3 m long and 0.5 m wide (wider than the slice), with
+    n_grousers transverse grousers 43 mm deep and 25.5 mm long at the bottom;
+    it starts clear above the particles (placed by the caller).  Material of
+    Sec. 3.1 (dry sand: 2200 kg/m^3, E 1 GPa, nu 0.15, mu_t 0.3, mu_r 0.02);
+    the plate takes the interparticle coefficients (Sec. 3.3)."""
+    lx, ly, depth = SLICE["lx"], SLICE["ly"], SLICE["depth"]
+    if d_max is None or d_max <= d_min:
+        layers = [(d_min / 2, depth)]
+        name = f"shear slice, uniform d {d_min * 1e3:.1f} mm"
+    else:
+        layers = graded_layers(d_min / 2, eta * d_min, growth, cap_ratio=d_max / d_min, depth=depth)
+        name = (f"shear slice, refined d {d_min * 1e3:.1f} -> {d_max * 1e3:.1f} mm, growth {growth}, eta {eta}, "
+                f"gamma {(growth - 1) / (growth * eta):.3f}")
+    x, r = layered_bed(lx, ly, layers, spread=0.1, phi=phi, seed=seed)
+    geoms = open_box_walls(lx, ly)
+    cx, cy, z_plate = plate_x, ly / 2, depth + 1.0
+    mat = Material(rho=RHO_PAPER, mu_t=MU_T_PAPER, mu_r=MU_R_PAPER)
+    parts = [GeomSpec(BOX, (cx, cy, z_plate), he=(0.15, 0.25, t_plate / 2), mu_t=mat.mu_t, mu_r=mat.mu_r)]
+    offs = np.linspace(-0.15 + L_GROUSER / 2, 0.15 - L_GROUSER / 2, n_grousers) if n_grousers > 1 else [0.0]
+    for gx in offs:
+        parts.append(GeomSpec(BOX, (cx + float(gx), cy, z_plate - t_plate / 2 - H_GROUSER / 2),
+                              he=(L_GROUSER / 2, 0.25, H_GROUSER / 2), mu_t=mat.mu_t, mu_r=mat.mu_r))
+    first = len(geoms)
+    geoms.extend(parts)
+    return Bed(x, r, geoms, mat, name=name, plate=first, plate_parts=tuple(range(first, len(geoms))),
+               box=(lx, ly, depth))
+
+
+def shear_slice_layers(d_min, d_max, growth, eta, depth=0.6):
+    """(layers bottom up, refined depth z_max) of shear_slice's refined bed, for Eq. 10."""
+    layers = graded_layers(d_min / 2, eta * d_min, growth, cap_ratio=d_max / d_min, depth=depth)
+    zmax = sum(t for r, t in layers[1:])
+    return layers, zmax
+
+
 def random_cloud(n, seed, rmin=2e-3, rmax=6e-3, box=0.05, overlap_ok=False, vscale=0.0):
     """Spheres placed uniformly at random in [-box, box]^3 (overlaps allowed
     unless overlap_ok is False, then rejection sampled); velocities uniform in

@@ -912,6 +912,20 @@ extern "C" dem_status dem_apply_plate_velocity(dem_bed* b, int32_t g, const doub
     return DEM_OK;
 }
 
+extern "C" dem_status dem_set_plate_load(dem_bed* b, int32_t g, const double force[3]) {
+    g_err.clear();
+    if (!b || !force) return fail(DEM_ERR_ARG, "NULL argument");
+    if (g < 0 || g >= b->n_geom) return fail(DEM_ERR_ARG, "geom %d out of range", g);
+    if (b->geom_group[g] < 0) return fail(DEM_ERR_ARG, "geom %d is in no load-driven group", g);
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(force[k])) return fail(DEM_ERR_ARG, "non-finite force");
+    CK(cudaSetDevice(b->dev));
+    const float f[3] = {(float)force[0], (float)force[1], (float)force[2]};
+    // a pageable source is staged before the call returns
+    CK(cudaMemcpyAsync(b->B.grp[b->geom_group[g]].force, f, sizeof f, cudaMemcpyHostToDevice, b->stream));
+    return DEM_OK;
+}
+
 // the primitives of one group: their bed's sweep count
 static int group_bed_nit(const dem_bed* b, int g) {
     for (const LevelGrid& l : b->levels)

@@ -26,7 +26,8 @@ PLANE, BOX, CYLINDER = 0, 1, 2
 # every entry point declared in include/dem.h
 EXPORTS = ("dem_create_bed", "dem_create_batch", "dem_autotune", "dem_step", "dem_apply_plate_velocity", "dem_read_forces",
            "dem_read_state", "dem_read_contacts", "dem_read_geom", "dem_sync", "dem_get_info",
-           "dem_set_timing", "dem_read_timing", "dem_set_params", "dem_apply_plate_load", "dem_record", "dem_step_adjoint",
+           "dem_set_timing", "dem_read_timing", "dem_set_params", "dem_apply_plate_load", "dem_set_plate_load",
+           "dem_record", "dem_step_adjoint",
            "dem_checkpoint_save", "dem_checkpoint_restore", "dem_checkpoint_free",
            "dem_destroy_bed", "dem_detect_contacts_noalloc", "dem_last_error")
 
@@ -114,6 +115,7 @@ def load(build: bool = True):
         "dem_read_timing": (i32, [vp, dp, dp, C.POINTER(C.c_int64)]),
         "dem_set_params": (i32, [vp, C.POINTER(dem_bed_desc)]),
         "dem_apply_plate_load": (i32, [vp, vp, i32, C.c_double, dp, i32]),
+        "dem_set_plate_load": (i32, [vp, i32, dp]),
         "dem_record": (i32, [vp, i32, i32, vp]),
         "dem_step_adjoint": (i32, [vp, vp, dp]),
         "dem_checkpoint_save": (i32, [vp, C.POINTER(vp)]),
@@ -299,6 +301,12 @@ class Bed:
         g = np.ascontiguousarray(np.atleast_1d(geoms), np.int32)
         f = (C.c_double * 3)(*map(float, force))
         _check(self.lib.dem_apply_plate_load(self._handle, _ptr(g), len(g), float(mass), f, int(dof)))
+
+    def set_plate_load(self, g, force):
+        """New external force [N] of the load-driven group holding primitive g
+        (dem_set_plate_load), from the next step on."""
+        f = (C.c_double * 3)(*map(float, force))
+        _check(self.lib.dem_set_plate_load(self._handle, int(g), f))
 
     def read_forces(self, g):
         f = (C.c_double * 3)()

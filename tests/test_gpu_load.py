@@ -167,3 +167,27 @@ def test_plate_load_errors():
     with pytest.raises(DemError):                          # no adjoint through a dynamic plate
         g.record(2, 1)
     g.close()
+
+
+def test_load_ramp_tracks_oracle():
+    # the normal load applied gradually (dem_set_plate_load between steps)
+    x, r, geoms, p, gi, load = loaded_case(n=1500, seed=21)
+    g = make_gpu(x, r, p, geoms)
+    o = make_oracle(x, r, p, geoms)
+    g.apply_plate_load([gi], load["mass"], (0.0, 0.0, 0.0), 4)
+    o.set_load([gi], load["mass"], (0.0, 0.0, 0.0), 4)
+    for k in range(40):
+        F = (0.0, 0.0, -2.0 * (k + 1))      # exact in FP32
+        g.set_plate_load(gi, F)
+        o.set_load_force(gi, F)
+        g.step(1)
+        o.step(1)
+    pg, po = g.read_geom(gi), o.geom(gi)
+    assert abs(pg.v[2] - po.v[2]) < 1e-4 * max(abs(po.v[2]), 1e-3)
+    _, vg, _ = g.read_state()
+    _, vo, _ = o.state()
+    assert np.abs(vg - vo).max() < 1e-4 * np.abs(vo).max()
+    from paper_2501_05300_gb300.dem import DemError
+    with pytest.raises(DemError):
+        g.set_plate_load(0, (0.0, 0.0, -1.0))      # a wall: in no group
+    g.close()

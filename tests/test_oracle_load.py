@@ -8,6 +8,7 @@ impulse-momentum balance of particles plus plate.
 import math
 
 import numpy as np
+import pytest
 
 from oracle import Geom, Oracle, OracleParams
 from oracle.binding import PLANE
@@ -113,3 +114,24 @@ def test_group_moves_with_its_members():
     assert ga.v == gb.v                              # one body
     assert abs(ga.c[2] - 1.0 - (gb.c[2] - 2.0)) < 1e-15
     assert ga.v[0] == 0.1                            # the first member's motor speed
+
+
+def test_load_force_changed_between_steps_free_fall():
+    # a group in free flight (no contacts, no gravity on it): v_k = sum_j dt F_j / M
+    # and z_k = z_0 + dt sum_j v_j, whatever the force does from step to step
+    h, M = 1e-4, 2.0
+    p = OracleParams(dt=h, n_it=5, gravity=(0.0, 0.0, 0.0))
+    plate = Geom(PLANE, c=(0.0, 0.0, 1.0), R=(1, 0, 0, 0, -1, 0, 0, 0, -1))
+    o = Oracle(p, np.array([[5.0, 5.0, -5.0]]), np.array([0.005]), geoms=[plate])
+    o.set_load([0], M, (0.0, 0.0, 0.0), 4)
+    forces = [-(k + 1) * 3.0 for k in range(20)]
+    v, z = 0.0, 1.0
+    for F in forces:
+        o.set_load_force(0, (0.0, 0.0, F))
+        o.step(1)
+        v += h * F / M
+        z += h * v
+    g = o.geom(0)
+    assert abs(g.v[2] - v) < 1e-14 and abs(g.c[2] - z) < 1e-14
+    with pytest.raises(ValueError):
+        Oracle(p, np.array([[5.0, 5.0, -5.0]]), np.array([0.005]), geoms=[plate]).set_load_force(0, (0, 0, 1))

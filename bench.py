@@ -860,6 +860,72 @@ def run_calibrate(args, max_iter=8, rtol=0.005):
                 seconds_per_gradient=el / len(hist), window_steps=steps)
 
 
+PHI_PAPER = 33.6           # triaxial friction angle of the paper's beds (Table 1: 33.5-33.7 deg)
+MC_STRAIN = 0.04           # axial strain of the calibration window
+
+
+def run_calibrate_mc(args, max_iter=8, rtol=0.005):
+    """Mohr-Coulomb calibration against the paper's triaxial friction angle
+    (Table 1): the 50k cell with Sec. 3.1's coefficients (mu_t 0.3, mu_r 0.02)
+    is sheared with servoed side walls to 4 % axial strain; from there, with
+    the side walls held, mu_t is adjusted by Newton steps with dJ/dmu_t from
+    the adjoint until J = mean(sigma_1 - K sigma_3) over the 400-step window is
+    zero, K = (1 + sin phi) / (1 - sin phi) for phi = 33.6 deg and no cohesion
+    (the failure line through the origin).  The state at 4 % strain is the one
+    reached with mu_t 0.3: the calibration is local to the window."""
+    import torch
+    from paper_2501_05300_gb300 import dem
+    from paper_2501_05300_gb300.adjoint import CellGeometry, geom_forces, principal_stresses
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    steps, every = args.triax_steps, args.triax_ckpt
+    spec = beds.triaxial_cell(TRIAX_N, seed=2505)
+    spec.material.mu_t, spec.material.mu_r = beds.MU_T_PAPER, beds.MU_R_PAPER
+    bed, prep = prepare_triaxial(dem, lanes=max(args.lanes, 0), spec=spec)
+    side = [beds.WALL_XLO, beds.WALL_XHI, beds.WALL_YLO, beds.WALL_YHI]
+    sig, L = _wall_stress(bed)
+    h0 = float(L[2])
+    n_shear = 0
+    while 1.0 - float(L[2]) / h0 < MC_STRAIN:
+        sig, L = _servo(bed, side, TRIAX_SIGMA, 0.05)
+        bed.apply_plate_velocity(beds.PLATEN, (0.0, 0.0, -TRIAX_RATE * float(L[2])))
+        bed.step(20)
+        n_shear += 20
+        sig, L = _wall_stress(bed)
+    for g in side:
+        bed.apply_plate_velocity(g, (0.0, 0.0, 0.0))
+    bed.step(args.warmup)
+    start = bed.save_checkpoint()
+    cell = CellGeometry.from_bed(bed)
+    s = math.sin(math.radians(PHI_PAPER))
+    K = (1.0 + s) / (1.0 - s)
+    theta = [1.0, beds.MU_T_PAPER, beds.MU_R_PAPER]
+    hist = []
+    t0 = time.perf_counter()
+    for k in range(max_iter):
+        bed.restore_checkpoint(start)
+        th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        F = geom_forces(bed, th, steps, every)
+        s1, s3 = principal_stresses(F, cell)
+        J = (s1 - K * s3).mean()
+        J.backward()
+        g = float(th.grad[1])
+        m1, m3 = float(s1.mean()), float(s3.mean())
+        phi = math.degrees(math.asin((m1 - m3) / (m1 + m3)))
+        hist.append({"mu_t": theta[1], "J_Pa": float(J.detach()), "dJ_dmu_t": g, "phi_deg": phi,
+                     "sigma1_kPa": m1 / 1e3, "sigma3_kPa": m3 / 1e3})
+        if abs(float(J.detach())) <= rtol * abs(m1) or g == 0.0:
+            break
+        theta[1] = float(np.clip(theta[1] - float(J.detach()) / g, 0.02, 2.0))
+    el = time.perf_counter() - t0
+    bed.free_checkpoint(start)
+    n = bed.n
+    bed.close()
+    return dict(target_phi_deg=PHI_PAPER, K=K, window_strain=MC_STRAIN, shear_steps=n_shear, particles=n,
+                history=hist, iterations=len(hist), mu_t=hist[-1]["mu_t"], phi_deg=hist[-1]["phi_deg"],
+                seconds_per_gradient=el / len(hist), window_steps=steps)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -879,6 +945,9 @@ def main():
                     help="with --protocol: multiplies every phase time (1 = the paper's 5.4 s)")
     ap.add_argument("--impact", action="store_true",
                     help="the settling box without and with the Newton impact stage")
+    ap.add_argument("--calibrate-mc", action="store_true",
+                    help="mu_t calibrated to the paper's triaxial friction angle (Mohr-Coulomb, no cohesion) "
+                         "with adjoint gradients")
     ap.add_argument("--solvers", action="store_true",
                     help="Jacobi against coloured Gauss-Seidel: iterations to tolerance on the refined bed")
     ap.add_argument("--triaxial", action="store_true",
@@ -940,6 +1009,15 @@ def main():
                           "config": {"workload": "pressure-sinkage and shear-displacement test of a grousered "
                                                  "plate under 2550 N on a 1.5 x 0.17 x 0.6 m slice (Sec. 3.3), "
                                                  "phase times x %g, dt 1e-4 s" % r["time_scale"], **r}}))
+        return
+    if args.calibrate_mc:
+        r = run_calibrate_mc(args)
+        print(json.dumps({"metric": "friction angle after calibration |phi - phi_paper|", "unit": "deg",
+                          "value": abs(r["phi_deg"] - r["target_phi_deg"]), "higher_is_better": False,
+                          "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": "50k triaxial cell, Sec. 3.1 coefficients, sheared to 4 % axial "
+                                                 "strain at 100 kPa; mu_t by Newton steps with adjoint gradients "
+                                                 "of mean(sigma_1 - K sigma_3) over 400 steps", **r}}))
         return
     if args.impact:
         r = run_impact(args)

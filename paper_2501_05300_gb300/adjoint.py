@@ -67,8 +67,8 @@ class CellGeometry:
         return cls(lo, hi, v, bed.dt)
 
 
-def deviatoric_stress(F, cell: CellGeometry):
-    """sigma_1 - sigma_3 in every step [Pa]: sigma_1 the platen's normal force
+def principal_stresses(F, cell: CellGeometry):
+    """(sigma_1, sigma_3) in every step [Pa]: sigma_1 the platen's normal force
     over its area, sigma_3 the mean normal stress on the four side walls, with
     the walls where they stand in that step (they move kinematically)."""
     steps = F.shape[0]
@@ -84,4 +84,10 @@ def deviatoric_stress(F, cell: CellGeometry):
     s1 = F[:, _beds.PLATEN, 2] / a_z
     s3 = 0.25 * ((F[:, _beds.WALL_XHI, 0] - F[:, _beds.WALL_XLO, 0]) / a_x +
                  (F[:, _beds.WALL_YHI, 1] - F[:, _beds.WALL_YLO, 1]) / a_y)
+    return s1, s3
+
+
+def deviatoric_stress(F, cell: CellGeometry):
+    """sigma_1 - sigma_3 in every step [Pa] (see principal_stresses)."""
+    s1, s3 = principal_stresses(F, cell)
     return s1 - s3

@@ -215,8 +215,9 @@ dem_status dem_read_timing(dem_bed* bed, double* step_ms, double* jacobi_ms, int
 /* Change the solver and material settings of an existing bed between steps,
  * as between the generation and the test phases of Sec. 3.1 / 3.3 (reduced
  * friction while settling).  Taken from `desc`: dt, n_it, damp_steps, e_H,
- * mu_t, mu_r, gravity, kn_scale, eps_reg and lanes; every other field is
- * ignored.  The warm-start impulses of the last step are rescaled by
+ * mu_t, mu_r, gravity, kn_scale, eps_reg and lanes, and solver, restitution
+ * and impact_speed unless negative (negative keeps the current value); every
+ * other field is ignored.  The warm-start impulses of the last step are rescaled by
  * dt_new / dt_old so that they stand for the same forces, and the sinkage
  * reference of every primitive is re-taken from the current particle surface
  * (the test phase starts here).  Synchronises; the per-step graphs are rebuilt. */

@@ -39,6 +39,10 @@ DT = 1e-5
 PLATE_V = 0.01
 # refined bed: eta = 4, d 5 -> 40 mm, growth 2, z_max = 0.14 m, h = 0.25 m
 N_IT = rules.n_iterations(rules.network_length_refined(4.0, 5e-3, 40e-3, 2.0, 0.25, 0.14), 0.02)
+# DRAM bytes of one two-pass sweep of this workload (k_contact_pass + k_body_pass), from one ncu
+# capture of dram__bytes_read.sum + dram__bytes_write.sum with cold caches; stale (None) for any
+# other layout
+SWEEP_TRAFFIC_TWO_PASS = 52.58e6 + 1.59e6 + 42.69e6
 # algorithmic bytes of one Jacobi sweep (per contact: 48 B row data + 24 B
 # impulse read + 24 B written; per particle: v,w read, v*,w* read, v,w written)
 BYTES_PER_CONTACT = 96
@@ -1080,7 +1084,9 @@ def main():
                    "sweep_layout": "two-pass" if r["tuned"][0] == 0 else f"one kernel, {r['tuned'][0]} threads/particle",
                    "resort_every": r["tuned"][1], "launch_params": "autotuner"},
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
-                     "frac": r["achieved"] / r["peak"], "traffic": None,
+                     "frac": r["achieved"] / r["peak"],
+                     "traffic": SWEEP_TRAFFIC_TWO_PASS if r["tuned"][0] == 0 else None,
+                     "traffic_note": "ncu DRAM bytes of one sweep, caches flushed before each launch",
                      "kernel": ("k_contact_pass + k_body_pass (one projected Jacobi sweep)" if r["tuned"][0] == 0
                                 else f"k_sweep<{r['tuned'][0]}, 1> (one projected Jacobi sweep)"),
                      "sweep_us": 1e3 * r["sweep_ms"], "alg_bytes_per_sweep": r["alg_bytes"],

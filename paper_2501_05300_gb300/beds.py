@@ -335,6 +335,67 @@ def shear_slice(d_min=8.5e-3, d_max=None, growth=1.25, eta=2.0, seed=2507, phi=0
                box=(lx, ly, depth))
 
 
+def radial_zones(d_min, growth, eta, d_max, extent):
+    """Zones (inner, outer distance, diameter) of a radially refined bed: zone n
+    holds diameter d_n = d_min growth^n (capped at d_max) in a shell eta d_n
+    thick, the layer rule of Sec. 2.1 applied to the distance from a point or
+    an axis instead of the depth (the hemispheric and radial zones Sec. 5
+    proposes); the capped size fills the rest out to `extent`."""
+    zones, rho, d = [], 0.0, d_min
+    while rho < extent:
+        if d >= d_max * (1 - 1e-9):
+            zones.append((rho, extent, d_max))
+            break
+        zones.append((rho, min(rho + eta * d, extent), d))
+        rho += eta * d
+        d = min(d * growth, d_max)
+    return zones
+
+
+def radially_refined_bed(lx=0.4, ly=0.4, depth=0.2, d_min=5e-3, growth=1.5, eta=3.0, d_max=20e-3,
+                         centre=None, mode="hemisphere", spread=0.1, seed=2508, gap=0.03):
+    """A bed refined around a point of its surface (mode "hemisphere": size
+    grows with the distance from the point, hemispheric zones) or around a
+    vertical axis through it (mode "cylinder": size grows with the horizontal
+    distance, radial zones), zones from radial_zones.  Each zone is a jittered
+    FCC lattice of its own size clipped to the zone, one radius (plus the
+    jitter) inside each zone boundary, so no two spheres overlap; it settles
+    under gravity like the layered beds.  Open box, frictionless walls."""
+    rng = np.random.default_rng(seed)
+    cx, cy = (lx / 2, ly / 2) if centre is None else centre
+    extent = math.sqrt(max(cx, lx - cx) ** 2 + max(cy, ly - cy) ** 2 + (depth ** 2 if mode == "hemisphere" else 0.0))
+    xs, rs = [], []
+    for lo, hi, d in radial_zones(d_min, growth, eta, d_max, extent):
+        r_nom = d / 2
+        rmax = r_nom * (1 + spread)
+        a = 2 * rmax * (1 + gap)
+        jit = 0.45 * (a - 2 * rmax)
+        m = rmax * 1.001 + jit
+        # an FCC lattice over the box, then the zone's points
+        dy, dz = a * math.sqrt(3.0) / 2.0, a * math.sqrt(2.0 / 3.0)
+        pts = []
+        for k in range(int((depth - 2 * m) / dz) + 1):
+            sx, sy = (k % 3) * a / 2.0, (k % 3) * a * math.sqrt(3.0) / 6.0
+            for j, y in enumerate(np.arange(m + sy, ly - m + 1e-12, dy)):
+                xr = np.arange(m + sx + (a / 2.0 if j % 2 else 0.0), lx - m + 1e-12, a)
+                pts.append(np.stack([xr, np.full_like(xr, y), np.full_like(xr, m + k * dz)], 1))
+        p = np.concatenate(pts) if pts else np.zeros((0, 3))
+        p = p + rng.uniform(-jit, jit, p.shape)
+        # distance from the point at the surface (or from the axis)
+        dh = np.hypot(p[:, 0] - cx, p[:, 1] - cy)
+        dist = np.hypot(dh, depth - p[:, 2]) if mode == "hemisphere" else dh
+        keep = (dist >= lo + m) & (dist <= hi - m) if lo > 0 else (dist <= hi - m)
+        if hi >= extent:
+            keep = dist >= lo + m
+        p = p[keep]
+        xs.append(p.astype(np.float64))
+        rs.append(_uniform_radii(rng, r_nom, len(p), spread))
+    x, r = np.concatenate(xs), np.concatenate(rs)
+    mat = Material(rho=RHO_PAPER, mu_t=MU_T_PAPER, mu_r=MU_R_PAPER)
+    return Bed(x, r, open_box_walls(lx, ly), mat, box=(lx, ly, depth),
+               name=f"{mode} refined bed d {d_min * 1e3:.1f} -> {d_max * 1e3:.1f} mm, growth {growth}, eta {eta}")
+
+
 def shear_slice_layers(d_min, d_max, growth, eta, depth=0.6):
     """(layers bottom up, refined depth z_max) of shear_slice's refined bed, for Eq. 10."""
     layers = graded_layers(d_min / 2, eta * d_min, growth, cap_ratio=d_max / d_min, depth=depth)

@@ -158,3 +158,25 @@ def test_set_params_keeps_state_and_rescales_warm_start():
     g2.sync()
     g1.close()
     g2.close()
+
+
+@pytest.mark.parametrize("mode", ["hemisphere", "cylinder"])
+def test_radially_refined_bed_settles_and_matches_the_oracle(mode):
+    # the radially refined generator on the GPU: one step against the oracle
+    # (contact set bit-exact), then settling under gravity stays finite and
+    # slows down
+    from dem_cases import canonical_gpu_contacts, make_gpu, make_oracle, params
+    b = beds.radially_refined_bed(lx=0.2, ly=0.2, depth=0.1, d_min=4e-3, d_max=12e-3, mode=mode)
+    p = params(n_it=60, rho=b.material.rho, mu_t=0.1, mu_r=0.01, dt=1e-4)
+    g = make_gpu(b.x, b.r, p, b.geoms)
+    o = make_oracle(b.x, b.r, p, b.geoms)
+    g.step(1)
+    o.step(1)
+    a, bb, lam, _ = g.read_contacts()
+    a, bb, lam, _ = canonical_gpu_contacts(a, bb, lam)
+    oa, ob, olam, _, _ = o.contacts()
+    assert np.array_equal(a, oa) and np.array_equal(bb, ob)
+    g.step(2000)
+    _, v, _ = g.read_state()
+    assert np.isfinite(v).all() and np.abs(v).max() < 1.0
+    g.close()

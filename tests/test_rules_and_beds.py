@@ -109,3 +109,33 @@ def test_refined_bed_radius_bands():
 def test_refined_bed_count_is_about_200k():
     b = beds.refined_sinkage_bed()
     assert 190_000 < b.n < 215_000
+
+
+def test_radial_zones_follow_the_layer_rule():
+    # the layer rule of Sec. 2.1 along a distance: d_n = growth d_{n-1},
+    # shells eta d_n thick, the capped size filling the rest
+    z = beds.radial_zones(5e-3, 1.5, 3.0, 20e-3, 0.35)
+    for (lo, hi, d), nxt in zip(z, z[1:]):
+        assert abs((hi - lo) - 3.0 * d) < 1e-12 and abs(nxt[0] - hi) < 1e-15
+        assert abs(nxt[2] - min(1.5 * d, 20e-3)) < 1e-15
+    assert z[-1][2] == 20e-3 and z[-1][1] == 0.35 and z[0] == (0.0, 0.015, 5e-3)
+
+
+@pytest.mark.parametrize("mode", ["hemisphere", "cylinder"])
+def test_radially_refined_bed_sizes_grow_with_distance_no_overlaps(mode):
+    b = beds.radially_refined_bed(mode=mode)
+    cx, cy, depth = 0.2, 0.2, 0.2
+    dh = np.hypot(b.x[:, 0] - cx, b.x[:, 1] - cy)
+    dist = np.hypot(dh, depth - b.x[:, 2]) if mode == "hemisphere" else dh
+    zones = beds.radial_zones(5e-3, 1.5, 3.0, 20e-3, 1.0)
+    for lo, hi, d in zones:
+        inside = (dist >= lo) & (dist < hi)
+        if inside.any():
+            # every sphere of a zone has that zone's size (10% spread)
+            assert (b.r[inside] >= 0.45 * d * 0.999).all() and (b.r[inside] <= 0.55 * d * 1.001).all()
+    # sizes grow monotonically with the zone index
+    assert np.corrcoef(dist, b.r)[0, 1] > 0.5
+    tree = cKDTree(b.x)
+    pairs = tree.query_pairs(2 * float(b.r.max()), output_type="ndarray")
+    gap = np.linalg.norm(b.x[pairs[:, 0]] - b.x[pairs[:, 1]], axis=1) - (b.r[pairs[:, 0]] + b.r[pairs[:, 1]])
+    assert gap.min() > 0

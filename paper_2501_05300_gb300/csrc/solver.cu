@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(SV_T, 12) k_contact_pass(SimParams P, DevBuf B
 // BT lanes per body: lane l adds the body's shares l, l+BT, ...; the lane sums
 // are combined by a fixed butterfly, so the result does not depend on timing.
 #define BT 1
-// 12 resident blocks per SM (42 registers): measured 2 % faster per sweep than
+// 12 resident blocks per SM (40 registers): measured 2 % faster per sweep than
 // the unbounded 56-register build on the refined bed; 16 (32 registers) spills
 __global__ void __launch_bounds__(SV_T, 12) k_body_pass(SimParams P, DevBuf B, int p, int it, int nact) {
     pdl_wait();

@@ -393,7 +393,7 @@ int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s
 static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 static __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
-// 12 resident blocks per SM (42 registers): the pass is latency-bound, more
+// 12 resident blocks per SM (40 registers): the pass is latency-bound, more
 // warps in flight beat the few spilled bytes
 __global__ void __launch_bounds__(SV_T, 12) k_contact_pass(SimParams P, DevBuf B, int p, int it, int nact) {
     pdl_wait();

@@ -238,6 +238,24 @@ def run_fine(args):
                 plate_force_N=[fx, fz], plate_z=zs)
 
 
+def rank_max(x, device="cpu"):
+    """The largest value of x over the ranks (the slowest rank sets the job's
+    time); x itself on one process."""
+    import torch
+    if not torch.distributed.is_available() or not torch.distributed.is_initialized():
+        return float(x)
+    if torch.distributed.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job rate: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_2501_05300_gb300 import dem
@@ -283,19 +301,15 @@ def run_gpu(args, rank, world):
     info = bed.info()
     contacts = info.contacts + info.geom_contacts
     f, t, sink = bed.read_forces(pl)
-    ms_per_step = step_ms / max(tsteps, 1)
-    if world > 1:
-        tt = torch.tensor([ms_per_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_per_step = float(tt.item())
-    value = world * n / (ms_per_step * 1e-3)
+    ms_per_step = rank_max(step_ms / max(tsteps, 1), dev)
+    value = job_throughput(n, world, ms_per_step * 1e-3)
     # dominant kernel: one Jacobi sweep
     sweep_ms = jac_ms / max(tsteps * N_IT, 1)
     alg_bytes = BYTES_PER_CONTACT * contacts + BYTES_PER_BODY * n
     achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
-    resorts = sum(1 for s in range(info.steps - args.steps, info.steps) if s % 20 == 0)
+    resorts = sum(1 for s in range(info.steps - args.steps, info.steps) if s % tuned[1] == 0)
     launches = args.steps * info.kernels_per_step + resorts * info.kernels_per_resort
 
     # end to end through the C ABI with host buffers: plate command in, force out
@@ -306,8 +320,8 @@ def run_gpu(args, rank, world):
         bed.apply_plate_velocity(pl, (0.0, 0.0, -PLATE_V))
         bed.step(1)
         bed.read_forces(pl)
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * n * e2e_steps / e2e_s
+    e2e_s = rank_max(time.perf_counter() - t0, dev)
+    e2e_value = job_throughput(n * e2e_steps, world, e2e_s)
     bed.close()
     return dict(value=value, ms_per_step=ms_per_step, n=n, contacts=contacts, sweep_ms=sweep_ms,
                 alg_bytes=alg_bytes, achieved=achieved, peak=peak, launches=launches,

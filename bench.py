@@ -622,7 +622,7 @@ PROTO_BEDS = (("reference: uniform d 8.5 mm", {}),
 
 def protocol_one(dem, label, cfg, scale, settle_steps):
     """One bed through the pressure-sinkage and shear-displacement test of
-    Sec. 3.3 with every phase time multiplied by `scale`: phase I the plate
+    Sec. 3.3 with every phase's duration multiplied by `scale`: phase I the plate
     under F_N = 2550 N (vertical dynamics, weight included), the load raised
     linearly over the first `load_ramp` of phase I; from t1 the pull speed
     ramps 0 -> 0.1 m/s over `ramp`, then holds to t_end.  Samples the plate's
@@ -632,10 +632,15 @@ def protocol_one(dem, label, cfg, scale, settle_steps):
     spec = beds.shear_slice(**cfg)
     m = spec.material
     d_min = 8.5e-3
-    bed = dem.Bed(spec.x, spec.r, geoms=spec.geoms, rho=m.rho, mu_t=0.1, mu_r=0.01, n_it=100, dt=2e-4, lanes=0)
+    # generation: compacted without friction, then relaxed with the generation
+    # friction of Sec. 3.1 (a lattice settled with friction stays loose)
+    bed = dem.Bed(spec.x, spec.r, geoms=spec.geoms, rho=m.rho, mu_t=0.0, mu_r=0.0, n_it=100, dt=2e-4, lanes=0)
     bed.step(settle_steps)
+    bed.set_params(dt=2e-4, n_it=100, mu_t=0.1, mu_r=0.01, lanes=0)
+    bed.step(1000)
     x, _, _ = bed.read_state()
     h = float((x[:, 2] + spec.r).max())
+    solid = float((4.0 / 3.0 * np.pi * spec.r.astype(np.float64) ** 3).sum() / (beds.SLICE["lx"] * beds.SLICE["ly"] * h))
     if cfg:
         _, zmax = beds.shear_slice_layers(d_min, cfg["d_max"], cfg["growth"], cfg["eta"])
         n_d = rules.network_length_refined(cfg["eta"], d_min, cfg["d_max"], cfg["growth"], h, zmax)
@@ -662,8 +667,12 @@ def protocol_one(dem, label, cfg, scale, settle_steps):
     bed.apply_plate_load(parts, P["mass"], (0.0, 0.0, 0.0), dof=4)
     z_surface = top
     tip_off = bed.read_geom(parts[0]).c[2] - min(bed.read_geom(g).c[2] - spec.geoms[g].he[2] for g in parts[1:])
-    t1, ramp, t_end = P["t1"] * scale, P["ramp"] * scale, P["t_end"] * scale
-    t_load = P["load_ramp"] * scale
+    # `scale` shortens the three phases; the load and speed ramps keep their
+    # own durations (a plate loaded faster plunges into the bed)
+    t_load, ramp = P["load_ramp"], P["ramp"]
+    t1 = max(P["t1"] * scale, t_load + 0.1)
+    t2 = t1 + max((P["t2"] - P["t1"]) * scale, ramp)
+    t_end = t2 + (P["t_end"] - P["t2"]) * scale
     f_now = 0.0
     n_steps = int(round(t_end / dt))
     every = max(1, int(round(1e-3 / dt)))
@@ -698,9 +707,10 @@ def protocol_one(dem, label, cfg, scale, settle_steps):
     t, sink, ft = a[:, 0], a[:, 1], a[:, 2]
     tr = ft / P["F_N"]
     in1 = t <= t1
-    in2 = (t > t1) & (t <= P["t2"] * scale)
+    in2 = (t > t1) & (t <= t2)
     in23 = t > t1
-    return dict(bed=label, particles=int(spec.n), n_it=nit, sweep_layout=info.lanes, steps=n_steps,
+    return dict(bed=label, particles=int(spec.n), solid_fraction=solid, n_it=nit, sweep_layout=info.lanes,
+                steps=n_steps,
                 ms_per_step=wall / n_steps * 1e3,
                 static_sinkage_m=float(sink[in1][-1]), dynamic_sinkage_m=float(sink[-1]),
                 peak_traction=float(tr[in2].max()), avg_traction=float(tr[in23].mean()),
@@ -719,7 +729,7 @@ def run_protocol(args):
     torch.cuda.set_device(0)
     torch.cuda.set_stream(torch.cuda.Stream())
     scale = args.protocol_scale
-    runs = [protocol_one(dem, label, cfg, scale, 2 * args.settle) for label, cfg in PROTO_BEDS]
+    runs = [protocol_one(dem, label, cfg, scale, 3 * args.settle // 2) for label, cfg in PROTO_BEDS]
     ref = runs[0]
     for r in runs[1:]:
         e = [(r["static_sinkage_m"] - ref["static_sinkage_m"]) / beds.H_GROUSER,
@@ -960,7 +970,7 @@ def main():
                     help="the pressure-sinkage / shear-displacement test (phases I-III) on the reference and "
                          "three refined slices")
     ap.add_argument("--protocol-scale", type=float, default=1.0,
-                    help="with --protocol: multiplies every phase time (1 = the paper's 5.4 s)")
+                    help="with --protocol: multiplies the duration of every phase, not the load and speed ramps (1 = the paper's 5.4 s)")
     ap.add_argument("--impact", action="store_true",
                     help="the settling box without and with the Newton impact stage")
     ap.add_argument("--calibrate-mc", action="store_true",
@@ -1026,7 +1036,7 @@ def main():
                           "dtype": "f32", "data": "synthetic",
                           "config": {"workload": "pressure-sinkage and shear-displacement test of a grousered "
                                                  "plate under 2550 N on a 1.5 x 0.17 x 0.6 m slice (Sec. 3.3), "
-                                                 "phase times x %g, dt 1e-4 s" % r["time_scale"], **r}}))
+                                                 "phase durations x %g (ramps unscaled), dt 1e-4 s" % r["time_scale"], **r}}))
         return
     if args.calibrate_mc:
         r = run_calibrate_mc(args)

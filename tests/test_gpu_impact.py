@@ -137,3 +137,15 @@ def test_impact_arguments():
     with pytest.raises(DemError):
         g.record(2, 1)     # the adjoint does not reverse the impact stage
     g.close()
+
+
+def test_impact_stage_with_gauss_seidel_matches_oracle():
+    # the impact stage runs before either solver; with coloured Gauss-Seidel
+    # after it the step still matches the oracle's
+    x, r, geoms, v = impact_cloud(1200, 11)
+    p = params(n_it=40, restitution=0.5, impact_speed=0.3, solver=1)
+    g, o = both(x, r, p, geoms, v=v)
+    assert g.info().impacts == o.impacts() > 30
+    vg, vo = g.read_state()[1], o.state()[1]
+    assert np.abs(vg - vo).max() < 1e-5 * np.abs(vo).max()
+    g.close()

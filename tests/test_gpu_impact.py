@@ -149,3 +149,24 @@ def test_impact_stage_with_gauss_seidel_matches_oracle():
     vg, vo = g.read_state()[1], o.state()[1]
     assert np.abs(vg - vo).max() < 1e-5 * np.abs(vo).max()
     g.close()
+
+
+def test_impact_stage_enabled_between_steps():
+    # dem_set_params turns the stage on (graphs rebuilt, buffers allocated):
+    # the same trajectory as a bed created with it
+    x, r, geoms, v = impact_cloud(800, 13)
+    p_on = params(n_it=30, restitution=0.5, impact_speed=0.3)
+    a = make_gpu(x, r, p_on, geoms, v=v)
+    b = make_gpu(x, r, params(n_it=30), geoms, v=v)
+    keys = ("dt", "n_it", "mu_t", "mu_r", "damp_steps", "e_H", "gravity", "kn_scale", "eps_reg")
+    b.set_params(**{k: p_on[k] for k in keys}, restitution=0.5, impact_speed=0.3)
+    a.step(5)
+    b.step(5)
+    assert a.info().impacts == b.info().impacts
+    for u, w in zip(a.read_state(), b.read_state()):
+        assert np.array_equal(u, w)
+    b.set_params(**{k: p_on[k] for k in keys}, impact_speed=0.0)     # and off again
+    b.step(2)
+    assert b.info().impacts == 0
+    a.close()
+    b.close()

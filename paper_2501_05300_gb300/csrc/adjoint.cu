@@ -545,8 +545,7 @@ __global__ void __launch_bounds__(AD_T) k_adj_rows(SimParams P, TapeStep T, AdjB
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < T.nc; c += gridDim.x * blockDim.x) {
         const int a = T.c_self[c], b = T.c_other[c];
         const ARow R = pair_row(T.rec, c);
-        const float4 l0 = T.lamA[c];
-        const float2 l1 = T.lamB[c];
+        const float4 l0 = T.lamA[c];   // (the rolling part of lambda^0 does not depend on the rows)
         const VW sa = T.vw0[a], sb = T.vw0[b];
         const VW ga = gb[a], gbb = gb[b];
         const float3 tva = sa.v.w * f3(ga.v), twa = sa.w.w * f3(ga.w);

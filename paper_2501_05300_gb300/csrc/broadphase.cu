@@ -14,10 +14,13 @@
 // and sum rounded separately (no fused multiply-add).  An FP32 pre-test with a
 // tolerance tol that covers the rounding of the FP32 copies and of the FP32
 // arithmetic settles all but a thin band of pairs: d_f32 >= r_a + r_b + tol
-// rejects, d_f32 < r_a + r_b - 2 tol accepts (the double distance is then below
-// r_a + r_b - tol, and tol is tens of FP32 ulps of r_a + r_b, far above the
-// double predicate's rounding), and only the band in between is decided by
-// the FP64 predicate.  The contact set is the exact predicate's either way.
+// rejects, d_f32 < r_a + r_b - tol accepts, and only the band in between is
+// decided by the FP64 predicate.  tol bounds the FP32 distance's error with
+// more than a factor two to spare: the copies' rounding (<= 3.5 2^-24 of the
+// coordinates, moved up to 1.25x) plus a few ulps of r_a + r_b from the FP32
+// arithmetic, against tol = 10 2^-24 of the coordinates + 80 2^-24 r_max; so an
+// accepted pair's double distance is below r_a + r_b by far more than the
+// double predicate's rounding.  The contact set is the exact predicate's.
 #include "dem_internal.cuh"
 
 #define BP_T 128
@@ -158,10 +161,9 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
                         idj = B.id[j];
                         // same level: the lower id owns the pair
                         if (!(l == li && idj < idi)) {
-                            // FP32 accept: the double distance is below r_a + r_b - tol
-                            // here, far inside the exact predicate's rounding; only
-                            // the band around contact takes the FP64 test
-                            const float Rin = fmaxf(pi.w + pj.w - 2.0f * P.tol, 0.0f);
+                            // FP32 accept (see the header); only the band around
+                            // contact takes the FP64 test
+                            const float Rin = fmaxf(pi.w + pj.w - P.tol, 0.0f);
                             hit = d2 < Rin * Rin || exact_pair(xi, B.pos[j]);
                         }
                     }

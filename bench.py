@@ -620,6 +620,27 @@ PROTO_BEDS = (("reference: uniform d 8.5 mm", {}),
               ("high gamma 0.500: 8.5 -> 30 mm", dict(d_max=30e-3, growth=2.0, eta=1.0)))
 
 
+def protocol_measures(t, sink, ft, t1, t2, F_N):
+    """The paper's four measures from sampled curves (Sec. 3.3): static sinkage
+    at the end of phase I, dynamic sinkage at the end, peak traction F_T / F_N
+    in phase II (t1, t2], average traction over phases II-III (after t1)."""
+    tr = np.asarray(ft, np.float64) / F_N
+    t, sink = np.asarray(t, np.float64), np.asarray(sink, np.float64)
+    return dict(static_sinkage_m=float(sink[t <= t1][-1]), dynamic_sinkage_m=float(sink[-1]),
+                peak_traction=float(tr[(t > t1) & (t <= t2)].max()), avg_traction=float(tr[t > t1].mean()))
+
+
+def protocol_errors(run, ref, h_grouser, F_N, F_N_max):
+    """Normalised errors against the reference (Sec. 4): sinkage differences
+    over the grouser depth, traction-force differences over F_N,max; the
+    aggregate error is the mean of their magnitudes."""
+    e = dict(static_sinkage=(run["static_sinkage_m"] - ref["static_sinkage_m"]) / h_grouser,
+             dynamic_sinkage=(run["dynamic_sinkage_m"] - ref["dynamic_sinkage_m"]) / h_grouser,
+             peak_traction=(run["peak_traction"] - ref["peak_traction"]) * F_N / F_N_max,
+             avg_traction=(run["avg_traction"] - ref["avg_traction"]) * F_N / F_N_max)
+    return e, float(np.mean(np.abs(list(e.values()))))
+
+
 def protocol_one(dem, label, cfg, scale, settle_steps):
     """One bed through the pressure-sinkage and shear-displacement test of
     Sec. 3.3 with every phase's duration multiplied by `scale`: phase I the plate
@@ -704,17 +725,9 @@ def protocol_one(dem, label, cfg, scale, settle_steps):
     info = bed.info()
     bed.close()
     a = np.array(samples)
-    t, sink, ft = a[:, 0], a[:, 1], a[:, 2]
-    tr = ft / P["F_N"]
-    in1 = t <= t1
-    in2 = (t > t1) & (t <= t2)
-    in23 = t > t1
     return dict(bed=label, particles=int(spec.n), solid_fraction=solid, n_it=nit, sweep_layout=info.lanes,
-                steps=n_steps,
-                ms_per_step=wall / n_steps * 1e3,
-                static_sinkage_m=float(sink[in1][-1]), dynamic_sinkage_m=float(sink[-1]),
-                peak_traction=float(tr[in2].max()), avg_traction=float(tr[in23].mean()),
-                samples=len(samples))
+                steps=n_steps, ms_per_step=wall / n_steps * 1e3,
+                **protocol_measures(a[:, 0], a[:, 1], a[:, 2], t1, t2, P["F_N"]), samples=len(samples))
 
 
 def run_protocol(args):
@@ -732,13 +745,8 @@ def run_protocol(args):
     runs = [protocol_one(dem, label, cfg, scale, 3 * args.settle // 2) for label, cfg in PROTO_BEDS]
     ref = runs[0]
     for r in runs[1:]:
-        e = [(r["static_sinkage_m"] - ref["static_sinkage_m"]) / beds.H_GROUSER,
-             (r["dynamic_sinkage_m"] - ref["dynamic_sinkage_m"]) / beds.H_GROUSER,
-             (r["peak_traction"] - ref["peak_traction"]) * PROTO["F_N"] / PROTO["F_N"],
-             (r["avg_traction"] - ref["avg_traction"]) * PROTO["F_N"] / PROTO["F_N"]]
-        r["normalised_errors"] = dict(static_sinkage=e[0], dynamic_sinkage=e[1], peak_traction=e[2],
-                                      avg_traction=e[3])
-        r["aggregate_error"] = float(np.mean(np.abs(e)))
+        r["normalised_errors"], r["aggregate_error"] = protocol_errors(r, ref, beds.H_GROUSER, PROTO["F_N"],
+                                                                       PROTO["F_N"])
         r["particle_reduction"] = ref["particles"] / r["particles"]
         r["speedup"] = ref["ms_per_step"] / r["ms_per_step"]
     return dict(time_scale=scale, protocol=PROTO, runs=runs)

@@ -139,3 +139,58 @@ def test_radially_refined_bed_sizes_grow_with_distance_no_overlaps(mode):
     pairs = tree.query_pairs(2 * float(b.r.max()), output_type="ndarray")
     gap = np.linalg.norm(b.x[pairs[:, 0]] - b.x[pairs[:, 1]], axis=1) - (b.r[pairs[:, 0]] + b.r[pairs[:, 1]])
     assert gap.min() > 0
+
+
+def table2():
+    rows = [l.split() for l in open(os.path.join(GOLD, "table2_refined_beds.txt"))
+            if l.strip() and not l.startswith("#")]
+    return np.array(rows, dtype=float)
+
+
+def test_shear_slice_counts_match_tables_2_and_3():
+    # uniform slices (Table 3) at phi 0.636 in the 1.5 x 0.17 x 0.6 m container
+    # (Sec. 3.3) hold the paper's counts; the three refined slices of the
+    # shear protocol fall in Table 2's ranges for their d_max (5 % slack: the
+    # table rounds to thousands)
+    for d_mm, count, _, _ in table3():
+        n = beds.shear_slice(d_min=d_mm * 1e-3).n
+        assert abs(n / count - 1) < 0.06, (d_mm, n, count)
+    for row in table2():
+        d_max, g_lo, g_hi, c_lo, c_hi = row[1] * 1e-3, row[2], row[3], row[6], row[7]
+        cfg = {15e-3: dict(growth=1.1, eta=4.0), 22.5e-3: dict(growth=1.25, eta=2.0),
+               30e-3: dict(growth=2.0, eta=1.0)}[round(d_max, 4)]
+        gamma = rules.discrete_aggressiveness(cfg["growth"], cfg["eta"])
+        assert g_lo <= gamma <= g_hi
+        n = beds.shear_slice(d_max=d_max, **cfg).n
+        assert 0.95 * c_lo <= n <= 1.05 * c_hi, (d_max, n)
+
+
+def test_shear_slice_plate_dimensions():
+    # plate 300 mm long and 500 mm wide (wider than the 170 mm slice), grousers
+    # 43 mm deep and 25.5 mm long at the bottom (Sec. 3.3)
+    b = beds.shear_slice(d_max=30e-3, growth=2.0, eta=1.0)
+    plate, grousers = b.geoms[b.plate], [b.geoms[g] for g in b.plate_parts[1:]]
+    assert abs(2 * plate.he[0] - 0.3) < 1e-12 and abs(2 * plate.he[1] - 0.5) < 1e-12
+    assert len(grousers) == 3
+    for g in grousers:
+        assert abs(2 * g.he[2] - 0.043) < 1e-12 and abs(2 * g.he[0] - 0.0255) < 1e-12
+        # hanging from the plate's underside
+        assert abs((g.c[2] + g.he[2]) - (plate.c[2] - plate.he[2])) < 1e-12
+    assert b.box == (1.5, 0.17, 0.6)
+
+
+def test_protocol_measures_and_errors():
+    import bench
+    t = np.linspace(0.001, 5.4, 5400)
+    sink = np.where(t <= 2.5, 0.002 * t / 2.5, 0.002 + 0.01 * (t - 2.5) / 2.9)
+    ft = np.where(t <= 2.5, 0.0, np.where(t <= 3.0, 2550 * 0.3 * np.sin(np.pi * (t - 2.5) / 0.5), 2550 * 0.25))
+    m = bench.protocol_measures(t, sink, ft, 2.5, 3.0, 2550.0)
+    assert abs(m["static_sinkage_m"] - 0.002) < 1e-5 and abs(m["dynamic_sinkage_m"] - 0.012) < 1e-12
+    assert abs(m["peak_traction"] - 0.3) < 1e-4
+    after = t > 2.5
+    assert abs(m["avg_traction"] - float((ft[after] / 2550).mean())) < 1e-12
+    ref = dict(static_sinkage_m=0.001, dynamic_sinkage_m=0.010, peak_traction=0.25, avg_traction=0.2)
+    e, agg = bench.protocol_errors(m, ref, 0.043, 2550.0, 2550.0)
+    assert abs(e["static_sinkage"] - (m["static_sinkage_m"] - 0.001) / 0.043) < 1e-15
+    assert abs(e["peak_traction"] - (m["peak_traction"] - 0.25)) < 1e-15
+    assert abs(agg - np.mean(np.abs(list(e.values())))) < 1e-15

@@ -1,6 +1,7 @@
 """The benchmark's multi-process reduction (one replica bed per rank, no
 data-path collective): two gloo ranks on the CPU agree on the slowest rank's
 time and on the whole-job rate."""
+import json
 import os
 import socket
 
@@ -18,24 +19,25 @@ def _free_port():
     return port
 
 
-def _rank(rank, world, port, out):
+def _rank(rank, world, port, outdir):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
     t = bench.rank_max(1.5 + rank, "cpu")          # rank 1 is the slow one
     rate = bench.job_throughput(1000, world, t)
-    out[rank] = (t, rate)
+    with open(os.path.join(outdir, f"rank{rank}.json"), "w") as f:
+        json.dump([t, rate], f)
     dist.barrier()
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_take_the_slowest_time():
+def test_two_gloo_ranks_take_the_slowest_time(tmp_path):
+    # ranks are spawned (never forked from this multi-threaded process) and
+    # report through files
     world = 2
-    with mp.Manager() as m:
-        out = m.dict()
-        mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
-        got = dict(out)
-    assert got[0] == got[1] == (2.5, world * 1000 / 2.5)
+    mp.spawn(_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    got = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
+    assert got[0] == got[1] == [2.5, world * 1000 / 2.5]
 
 
 def test_single_process_is_the_identity():

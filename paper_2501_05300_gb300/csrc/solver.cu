@@ -15,11 +15,17 @@
 // G M~^{-1} G^T + Sigma with masses split over each body's contacts (m / n_b).
 // The body pass sets v = v* + M^{-1} sum_c G_c^T p_c with v* = v + dt g.
 //
-// Execution: one thread per body.  A body walks its incidence list (ordered by
-// the other body's stable id), recomputes each contact's update from the two
-// bodies' previous iterates -- the same arithmetic on the same inputs at both
-// ends, so both ends agree bit for bit -- writes it if it owns the contact and
-// adds its own share of the impulse.  One kernel per sweep, no atomics.
+// Execution, two layouts here (the resident one is in resident.cu), no atomics:
+// - two-pass (k_contact_pass + k_body_pass, chained by programmatic dependent
+//   launch): one thread per contact computes its update once and writes each
+//   body's impulse share; one thread per body sums its shares in incidence
+//   order and its geometry contacts;
+// - one kernel per sweep (k_sweep<T>): T threads per body walk its incidence
+//   list (ordered by the other body's stable id) and recompute each contact's
+//   update from the two bodies' previous iterates -- the same arithmetic on
+//   the same inputs at both ends, so both ends agree bit for bit -- write it
+//   if the body owns the contact, and add their own share of the impulse.
+// The contact update itself (sweep.cuh) is shared by every layout.
 #include <algorithm>
 
 #include "dem_internal.cuh"

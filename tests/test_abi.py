@@ -43,3 +43,25 @@ def test_binding_loads_without_gpu():
     assert b"desc" in lib.dem_last_error()
     assert lib.dem_step(None, 1) == dem.DEM_ERR_ARG
     assert lib.dem_destroy_bed(None) == dem.DEM_OK
+
+
+@pytest.mark.parametrize("name", ["dem_geom", "dem_bed_desc", "dem_info"])
+def test_struct_layouts_match_the_binding(name, tmp_path):
+    """Every field of the header's structs sits at the offset the ctypes
+    binding uses, and the sizes agree (a C program compiled against
+    include/dem.h prints them)."""
+    from paper_2501_05300_gb300 import dem
+    cls = getattr(dem, name)
+    fields = [f[0] for f in cls._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dem.h"', "int main(void) {",
+             f'  printf("size %zu\\n", sizeof({name}));']
+    lines += [f'  printf("{f} %zu\\n", offsetof({name}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(cls), name
+    for f in fields:
+        assert int(out[f]) == getattr(cls, f).offset, (name, f)

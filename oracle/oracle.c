@@ -681,7 +681,10 @@ static void step_once(orc_sim* s) {
             for (int q = 0; q < 3; ++q) {
                 c->n[q] = hh.n[q];
                 c->la[q] = -(ra - 0.5 * c->delta) * c->n[q];
-                c->lb[q] = (hh.q[q] + 0.5 * c->delta * c->n[q]) - geo->c[q];
+                /* lever from the primitive's centre to the middle of the
+                 * overlap, where the sphere's arm ends too: half the overlap
+                 * below the surface point q (n points out of the primitive) */
+                c->lb[q] = (hh.q[q] - 0.5 * c->delta * c->n[q]) - geo->c[q];
                 vb_lin[q] = geo->v[q];
                 vb_ang[q] = geo->w[q];
             }

@@ -63,9 +63,9 @@ __global__ void __launch_bounds__(IM_T) k_impact_rows(SimParams P, DevBuf B, Imp
         const GeoHit hh = geom_hit(G, xa.x, xa.y, xa.z, xa.w);
         const float delta = (float)hh.delta;
         const float3 n = make_float3((float)hh.n[0], (float)hh.n[1], (float)hh.n[2]);
-        const float3 lever = make_float3((float)(hh.q[0] - G.c[0]) + 0.5f * delta * n.x,
-                                         (float)(hh.q[1] - G.c[1]) + 0.5f * delta * n.y,
-                                         (float)(hh.q[2] - G.c[2]) + 0.5f * delta * n.z);
+        const float3 lever = make_float3((float)(hh.q[0] - G.c[0]) - 0.5f * delta * n.x,
+                                         (float)(hh.q[1] - G.c[1]) - 0.5f * delta * n.y,
+                                         (float)(hh.q[2] - G.c[2]) - 0.5f * delta * n.z);
         const float3 wg = make_float3((float)G.w[0], (float)G.w[1], (float)G.w[2]);
         const float3 vgp = make_float3((float)G.v[0], (float)G.v[1], (float)G.v[2]) + cross(wg, lever);
         const float kin = dot(n, vgp);

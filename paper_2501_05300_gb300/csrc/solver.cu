@@ -132,10 +132,12 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         const float delta = (float)hh.delta;
         const float3 n = make_float3((float)hh.n[0], (float)hh.n[1], (float)hh.n[2]);
         const float la = ra - 0.5f * delta;
-        // contact point in the middle of the overlap, lever from the primitive's centre
-        const float3 lever = make_float3((float)(qq[0] - G.c[0]) + 0.5f * delta * n.x,
-                                         (float)(qq[1] - G.c[1]) + 0.5f * delta * n.y,
-                                         (float)(qq[2] - G.c[2]) + 0.5f * delta * n.z);
+        // contact point in the middle of the overlap (where the sphere's arm
+        // ends: half the overlap below the surface point q, n pointing out of
+        // the primitive), lever from the primitive's centre
+        const float3 lever = make_float3((float)(qq[0] - G.c[0]) - 0.5f * delta * n.x,
+                                         (float)(qq[1] - G.c[1]) - 0.5f * delta * n.y,
+                                         (float)(qq[2] - G.c[2]) - 0.5f * delta * n.z);
         const float3 wg = make_float3((float)G.w[0], (float)G.w[1], (float)G.w[2]);
         const float3 vgp = make_float3((float)G.v[0], (float)G.v[1], (float)G.v[2]) + cross(wg, lever);
         const float dstar = 2.0f * ra;   // flat primitive: d_b -> infinity

@@ -13,12 +13,17 @@
 // sizeof(NoAllocScratch) ~ 8.4 MB on every GPU that loads the library, held
 // until the process exits.  Every call reuses the same array: calls that
 // overlap on the GPU (different streams, or different host threads, without
-// ordering) race and corrupt each other.
+// ordering) race and corrupt each other.  Radii must be positive and finite and
+// coordinates finite: otherwise no pair is written and *count receives -1.
+// The pair counter is 64-bit, so a dense input (every sphere in one cell) gives
+// its full pair count however large, and only the first cap pairs are written.
 //
 // Method: one uniform grid of cells 2 r_max wide, hashed into a fixed number of
 // buckets; particles are counting-sorted into buckets; each particle tests the
 // buckets of its 27 neighbour cells with the same exact FP64 predicate as the
 // per-step detection (geometry.cuh).  Output order is not specified.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "dem_internal.cuh"
@@ -37,14 +42,49 @@ struct NoAllocScratch {
     int scan_tmp[3 * (NA_BUCKETS / 2048 + 2)];
     unsigned rmax_bits;   // largest radius, as the bits of a positive float
     unsigned xmax_bits;   // largest |coordinate|, likewise
-    int npairs;
+    unsigned bad;         // nonzero: a radius not positive and finite, or a non-finite coordinate
+    unsigned pad;
+    unsigned long long npairs;   // pairs found (may exceed the caller's capacity)
 };
+
+// the per-call clear zeroes rmax_bits .. npairs as one range
+static_assert(offsetof(NoAllocScratch, npairs) == offsetof(NoAllocScratch, rmax_bits) + 4 * sizeof(unsigned),
+              "NoAllocScratch: the cleared header must be contiguous");
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-// host-side addresses of g_noalloc_scratch, one per device, looked up once
+// host-side addresses of g_noalloc_scratch, one per device, looked up once per
+// CUDA context: a device reset reloads the module, and the array may move
 static NoAllocScratch* g_scratch_addr[64];
+static unsigned long long g_scratch_ctx[64];
 static std::mutex g_scratch_mu;
+
+// unique id of the calling thread's current context (0 if it cannot be had);
+// the driver calls are reached through the runtime, so the library does not
+// link the driver library itself
+typedef CUresult (*PFN_ctx_current)(CUcontext*);
+typedef CUresult (*PFN_ctx_id)(CUcontext, unsigned long long*);
+static unsigned long long current_ctx_id() {
+    static PFN_ctx_current get_cur = nullptr;
+    static PFN_ctx_id get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = (PFN_ctx_current)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_ctx_id)f;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur && get_id && get_cur(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
 
 static __device__ __forceinline__ unsigned bucket_of(int cx, int cy, int cz) {
     return (((unsigned)cx * 73856093u) ^ ((unsigned)cy * 19349663u) ^ ((unsigned)cz * 83492791u)) &
@@ -61,17 +101,35 @@ __global__ void __launch_bounds__(NA_T) k_na_extent(NoAllocScratch* S, int n, co
                                                     const float* rad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    atomicMax(&S->rmax_bits, __float_as_uint(rad[i]));
-    const float ax = fmaxf(fabsf((float)pos[3 * i]), fmaxf(fabsf((float)pos[3 * i + 1]), fabsf((float)pos[3 * i + 2])));
+    const float r = rad[i];
+    const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    if (!(r > 0.0f) || !isfinite(r) || !isfinite(x) || !isfinite(y) || !isfinite(z)) {
+        S->bad = 1u;
+        return;
+    }
+    // positive floats order like their bit patterns
+    atomicMax(&S->rmax_bits, __float_as_uint(r));
+    const float ax = fmaxf(fabsf((float)x), fmaxf(fabsf((float)y), fabsf((float)z)));
     atomicMax(&S->xmax_bits, __float_as_uint(ax));
+}
+
+// Cell coordinates clamped to +-2^30, so that neighbour offsets never overflow
+// (clamping is monotone: two spheres' clamped coordinates are no further apart
+// than their true ones, so no touching pair is missed).
+#define NA_CLAMP (1 << 30)
+static __device__ __forceinline__ int na_coord(double x, float inv) {
+    const float f = (float)x * inv;
+    if (!(f > -(float)NA_CLAMP)) return -NA_CLAMP;   // NaN included (only with bad input)
+    if (!(f < (float)NA_CLAMP)) return NA_CLAMP;
+    return __float2int_rd(f);
 }
 
 static __device__ __forceinline__ void na_coords(const NoAllocScratch* S, const double* pos, int i, int& cx,
                                                  int& cy, int& cz) {
     const float inv = 1.0f / na_cell(S);
-    cx = __float2int_rd((float)pos[3 * i] * inv);
-    cy = __float2int_rd((float)pos[3 * i + 1] * inv);
-    cz = __float2int_rd((float)pos[3 * i + 2] * inv);
+    cx = na_coord(pos[3 * i], inv);
+    cy = na_coord(pos[3 * i + 1], inv);
+    cz = na_coord(pos[3 * i + 2], inv);
 }
 
 __global__ void __launch_bounds__(NA_T) k_na_count(NoAllocScratch* S, int n, const double* pos) {
@@ -95,7 +153,7 @@ __global__ void __launch_bounds__(NA_T) k_na_pairs(NoAllocScratch* S, int n, con
                                                    long long cap, int32_t* key_a, int32_t* key_b,
                                                    float* delta) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || S->bad) return;
     const float rmax = __uint_as_float(S->rmax_bits);
     const float tol = 4.0f * ldexpf(__uint_as_float(S->xmax_bits), -23) + 16.0f * ldexpf(rmax, -24);
     const double4_32a xi = make_double4_32a(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], (double)rad[i]);
@@ -126,8 +184,8 @@ __global__ void __launch_bounds__(NA_T) k_na_pairs(NoAllocScratch* S, int n, con
                     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
                     const double Rd = __dadd_rn(xi.w, xj.w);
                     const float dl = (float)__dsub_rn(__dmul_rn(Rd, Rd), d2) / ((float)Rd + sqrtf((float)d2));
-                    const int slot = atomicAdd(&S->npairs, 1);
-                    if (slot < cap) {
+                    const unsigned long long slot = atomicAdd(&S->npairs, 1ull);
+                    if (slot < (unsigned long long)cap) {
                         key_a[slot] = i;
                         key_b[slot] = j;
                         delta[slot] = dl;
@@ -136,7 +194,9 @@ __global__ void __launch_bounds__(NA_T) k_na_pairs(NoAllocScratch* S, int n, con
             }
 }
 
-__global__ void k_na_count_out(const NoAllocScratch* S, int64_t* count) { *count = S->npairs; }
+__global__ void k_na_count_out(const NoAllocScratch* S, int64_t* count) {
+    *count = S->bad ? (int64_t)-1 : (int64_t)S->npairs;
+}
 
 void dem_set_error_message(const char* msg);
 static dem_status na_fail(dem_status st, const char* msg);
@@ -154,20 +214,24 @@ extern "C" dem_status dem_detect_contacts_noalloc(int32_t n, const double* pos, 
     NoAllocScratch* S;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_addr[dev]) {
-            // first call on this device: the device address of the scratch array
+        const unsigned long long ctx = current_ctx_id();
+        if (!g_scratch_addr[dev] || (ctx != 0 && ctx != g_scratch_ctx[dev])) {
+            // first call on this device (or in a new context after a device
+            // reset): the device address of the scratch array
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) return na_fail(DEM_ERR_CUDA, cudaGetErrorString(e));
             g_scratch_addr[dev] = (NoAllocScratch*)p;
+            g_scratch_ctx[dev] = current_ctx_id();
         }
         S = g_scratch_addr[dev];
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // clear what must start at zero: histogram, fill cursors, extents, pair counter
+    // clear what must start at zero: histogram, fill cursors, extents, the
+    // invalid-input flag and the pair counter
     cudaMemsetAsync(S->count, 0, sizeof(S->count), s);
     cudaMemsetAsync(S->fill, 0, sizeof(S->fill), s);
-    cudaMemsetAsync(&S->rmax_bits, 0, 3 * sizeof(int), s);
+    cudaMemsetAsync(&S->rmax_bits, 0, 4 * sizeof(unsigned) + sizeof(unsigned long long), s);
     const int nb = n > 0 ? (n + NA_T - 1) / NA_T : 1;
     if (n > 0) {
         k_na_extent<<<nb, NA_T, 0, s>>>(S, n, pos, radius);

@@ -18,10 +18,19 @@
  *  - Every call returns a dem_status and never throws.  dem_last_error()
  *    returns a thread-local message describing the last failure.
  *  - dem_step only enqueues work on the bed's CUDA stream and returns.  Faults
- *    found on the device (contact capacity exceeded, non-finite state) are
- *    latched in a device flag; the next synchronising call (dem_read_*,
- *    dem_sync) returns them, and the bed then refuses to step (DEM_ERR_STATE)
- *    until it is destroyed.
+ *    found on the device are latched in a device flag, and while it is set no
+ *    kernel changes the bed: the step that faulted and the steps enqueued after
+ *    it are not committed.  The next synchronising call (dem_read_*, dem_sync,
+ *    dem_get_info, checkpoints) handles them:
+ *      - contact storage exceeded (the total, or one particle's list): the
+ *        arrays grow to what the step needed and the uncommitted steps run
+ *        again, with the plate velocities and loads current at that call; the
+ *        results equal those of a bed created with enough capacity.  The call
+ *        then succeeds.  During dem_record / dem_step_adjoint an overflow is
+ *        reported instead (DEM_ERR_CAPACITY), as is one beyond 2^30 contacts;
+ *      - a non-finite velocity (DEM_ERR_NONFINITE) or a resident-sweep wait
+ *        that gave up (DEM_ERR_TIMEOUT) is returned, and the bed then refuses
+ *        to step (DEM_ERR_STATE) until it is destroyed.
  *  - Particles are identified by their index in the arrays given to
  *    dem_create_bed ("stable id").  The library reorders particles internally
  *    (Morton order) but every read returns stable-id order.
@@ -91,7 +100,8 @@ typedef struct dem_bed_desc {
     float delta_floor;          /* overlap floor in the Hertz Jacobian [m]; 0 = 1e-6 * d_min */
     int32_t n_geom;             /* number of primitives, >= 0 */
     const dem_geom* geom;       /* [n_geom], host memory */
-    int64_t contact_capacity;   /* sphere-sphere contacts; 0 = 8 n (grows never) */
+    int64_t contact_capacity;   /* sphere-sphere contacts held at first (0 = 8 n + 1024); the
+                                   arrays grow when a step overflows them (see Conventions) */
     int32_t resort_every;       /* Morton re-sort period in steps; 0 = 20 */
     float level_ratio;          /* radius ratio per grid level; 0 = 2 */
     int32_t lanes;              /* Jacobi sweep layout: 0 = contact pass + body pass (default);
@@ -302,15 +312,18 @@ dem_status dem_destroy_bed(dem_bed* bed);
  *   key_a, key_b [cap] int32, delta [cap] float: device memory; contact k is the
  *     pair (key_a[k] < key_b[k]) of input indices with overlap delta[k] > 0, found
  *     with the same exact predicate as dem_step; order unspecified.
- *   count: device int64, receives the number of contacts (may exceed cap; only
- *     the first cap are written).
+ *   count: device int64, receives the number of contacts (a 64-bit count: it may
+ *     exceed cap, and only the first cap contacts are written), or -1 when a
+ *     radius is not positive and finite or a coordinate is not finite (nothing
+ *     is written then).
  *   stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
  * Allocates nothing: every intermediate array lives in one static device array
  * of about 8.4 MB, present on every GPU that loads the library until the process
  * exits.  n must be <= 262144 (DEM_ERR_ARG otherwise).  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the array, so calls
- * that overlap on the GPU race: order them on one stream. */
+ * device, and the first call after a device reset, looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race:
+ * order them on one stream. */
 dem_status dem_detect_contacts_noalloc(int32_t n, const double* pos, const float* radius, int64_t cap,
                                        int32_t* key_a, int32_t* key_b, float* delta, int64_t* count,
                                        void* stream);

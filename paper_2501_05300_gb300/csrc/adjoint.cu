@@ -738,6 +738,21 @@ void dem_adjoint_release(dem_bed* b) {
     b->adj = nullptr;
 }
 
+void dem_adjoint_drop(dem_bed* b) {
+    AdjointState* S = b->adj;
+    if (!S) return;
+    auto fr = [&](void* p) { if (p) dem_dfree(b, p); };
+    for (Checkpoint& K : S->ck) fr(K.mem);
+    fr(S->end.mem);
+    for (TapeStep& T : S->tape) fr(T.mem);
+    fr(S->fhist); fr(S->cnt_dev); fr(S->wts);
+    for (int q = 0; q < 2; ++q) {
+        fr(S->xbar[q]); fr(S->sbar[q]); fr(S->vb[q]); fr(S->lw[q]); fr(S->glw[q]);
+    }
+    fr(S->vacc); fr(S->L); fr(S->A); fr(S->gL); fr(S->gA); fr(S->part); fr(S->grad);
+    dem_adjoint_release(b);
+}
+
 // ---------------------------------------------------------------------------
 // host: checkpoints
 // ---------------------------------------------------------------------------
@@ -796,6 +811,9 @@ static dem_status restore_checkpoint(dem_bed* b, const Checkpoint& K) {
     b->steps = K.steps;
     const int q = (int)((b->steps & 1) ^ 1);
     cudaStream_t s = b->stream;
+    // the device's count of committed steps follows the restored step number
+    const long long committed = K.steps;
+    DEM_CK(cudaMemcpyAsync(B.committed, &committed, sizeof committed, cudaMemcpyHostToDevice, s));
     auto cp = [&](void* dst, const void* src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
     };
@@ -956,6 +974,9 @@ extern "C" dem_status dem_checkpoint_save(dem_bed* b, dem_checkpoint** out) {
     *out = nullptr;
     if (b->faulted) return dem_fail(DEM_ERR_STATE, "the bed holds a latched device fault");
     DEM_CK(cudaSetDevice(b->dev));
+    // a pending overflow is repaired (its steps re-run) before the snapshot
+    dem_status st0 = dem_check_fault(b);
+    if (st0 != DEM_OK) return st0;
     dem_checkpoint* c = new dem_checkpoint();
     c->bed = b;
     const size_t ng = std::max(b->P.ng, 1);
@@ -983,7 +1004,10 @@ extern "C" dem_status dem_checkpoint_restore(dem_bed* b, const dem_checkpoint* c
     if (c->bed != b) return dem_fail(DEM_ERR_ARG, "the checkpoint belongs to another bed");
     if (b->faulted) return dem_fail(DEM_ERR_STATE, "the bed holds a latched device fault");
     DEM_CK(cudaSetDevice(b->dev));
-    dem_status st = restore_checkpoint(b, c->K);
+    // a pending overflow is repaired before the state is replaced
+    dem_status st = dem_check_fault(b);
+    if (st != DEM_OK) return st;
+    st = restore_checkpoint(b, c->K);
     if (st != DEM_OK) return st;
     const size_t ng = std::max(b->P.ng, 1);
     DEM_CK(cudaMemcpyAsync(b->B.gacc, c->gacc, 6 * ng * sizeof(long long), cudaMemcpyDeviceToDevice, b->stream));
@@ -1035,6 +1059,10 @@ extern "C" dem_status dem_record(dem_bed* b, int32_t nsteps, int32_t ckpt_every,
         if ((st = dem_dalloc(b, (void**)&S->cnt_dev, 2 * (size_t)nsteps * sizeof(int))) != DEM_OK) return st;
         S->cnt_n = 2 * (size_t)nsteps;
     }
+    // an overflow inside the window is reported, not repaired: the recorded
+    // forces and counts would mix the failed and the re-run steps
+    b->no_grow = true;
+    struct Restore { dem_bed* b; ~Restore() { b->no_grow = false; } } restore{b};
     for (int t = 0; t < nsteps; ++t) {
         if (t % ckpt_every == 0 && (st = save_checkpoint(b, S->ck[t / ckpt_every])) != DEM_OK) return st;
         const int p = (int)(b->steps & 1);
@@ -1076,6 +1104,9 @@ extern "C" dem_status dem_step_adjoint(dem_bed* b, const double* dJ_dF, double g
     if (memcmp(&S->P, &b->P, sizeof(SimParams)) != 0)
         return dem_fail(DEM_ERR_STATE, "solver settings changed since dem_record");
     if (b->steps != S->end.steps) return dem_fail(DEM_ERR_STATE, "the bed was stepped after dem_record");
+    // the reverse pass re-runs recorded steps at the recorded capacity: no growth
+    b->no_grow = true;
+    struct Restore { dem_bed* b; ~Restore() { b->no_grow = false; } } restore{b};
     if (S->P.ng > 0 && !dJ_dF) return dem_fail(DEM_ERR_ARG, "dJ_dF is NULL");
     DEM_CK(cudaSetDevice(b->dev));
     cudaStream_t s = b->stream;

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -205,6 +206,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     *out = nullptr;
     if (!descs || nbeds < 1) return fail(DEM_ERR_ARG, "desc is NULL or no beds");
     int64_t n64 = 0, ng64 = 0, cap_sum = 0;
+    bool cap_default = false;   // some bed takes the default capacity (then with a pad)
     for (int k = 0; k < nbeds; ++k) {
         dem_status st = check_desc(&descs[k], k);
         if (st != DEM_OK) return st;
@@ -213,6 +215,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
         n64 += descs[k].n;
         ng64 += descs[k].n_geom;
         cap_sum += descs[k].contact_capacity > 0 ? descs[k].contact_capacity : 8LL * descs[k].n;
+        cap_default |= descs[k].contact_capacity <= 0;
     }
     if (n64 > (int64_t)0x7fffffff / 8) return fail(DEM_ERR_ARG, "too many particles");
     if (ng64 > DEM_MAX_GEOM) return fail(DEM_ERR_ARG, "%lld primitives exceed %d", (long long)ng64, DEM_MAX_GEOM);
@@ -437,10 +440,12 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     P.mu_t = d->mu_t;
     P.mu_r = d->mu_r;
     P.gx = d->gravity[0]; P.gy = d->gravity[1]; P.gz = d->gravity[2];
-    int64_t cap = cap_sum + 1024;
+    int64_t cap = cap_sum + (cap_default ? 1024 : 0);
     if (cap > (int64_t)0x3fffffff) cap = 0x3fffffff;
     P.max_contacts = (int)cap;
     P.max_geo = 2 * n + 1024;
+    P.max_own = DEM_MAX_OWN;
+    P.max_geo_body = DEM_MAX_GEO;
     P.lanes = d->lanes;   // 0: two-pass sweep; 1, 2, 4, 8: one kernel, that many threads per body;
                           // 16: resident sweep where the bed takes it, else two-pass
     P.solver = d->solver;
@@ -456,6 +461,11 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     P.e_imp = d->restitution;
     P.v_imp = d->impact_speed;
     P.n_beds = nbeds;
+    P.spin_limit = DEM_SPIN_LIMIT;
+    if (const char* e = std::getenv("DEM_TEST_SPIN_LIMIT")) {
+        const long v = std::strtol(e, nullptr, 10);
+        if (v >= 1 && v <= (long)DEM_SPIN_LIMIT) P.spin_limit = (unsigned)v;
+    }
     for (int k = 1; k < nbeds && P.solver; ++k)
         if (descs[k].n_it != descs[0].n_it) {
             release(b);
@@ -505,17 +515,18 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     AL(B.lv, (size_t)L);
     AL(B.pos, N); AL(B.posr, N); AL(B.vw0, N); AL(B.vw[0], N); AL(B.vw[1], N);
     AL(B.id, N); AL(B.lvl, N); AL(B.prev_of, N); AL(B.resorted, 1); AL(B.err, 1);
-    AL(B.lvl_lo, 3 * (size_t)L); AL(B.lvl_hi, 3 * (size_t)L);
+    AL(B.committed, 1); AL(B.need, 2);
+    AL(B.lvl_lo, 3 * (size_t)L); AL(B.lvl_hi, 3 * (size_t)L); AL(B.tolv, 2);
     AL(B.body_cell, N); AL(B.cell_cnt, NC + 1); AL(B.cell_start, NC + 1); AL(B.cell_fill, NC + 1);
     AL(B.cell_body, N); AL(B.cell_pos, N);
-    AL(B.tmp_own, N * DEM_MAX_OWN); AL(B.tmp_geo, N * DEM_MAX_GEO);
+    AL(B.tmp_own, N * (size_t)P.max_own); AL(B.tmp_geo, N * (size_t)P.max_geo_body);
     AL(B.own_cnt, N + 1); AL(B.in_cnt, N + 1); AL(B.geo_cnt, N + 1); AL(B.in_fill, N + 1);
     AL(B.own_start[0], N + 1); AL(B.own_start[1], N + 1); AL(B.inc_start, N + 1);
     AL(B.geo_start[0], N + 1); AL(B.geo_start[1], N + 1);
     AL(B.c_other, C); AL(B.c_key[0], C); AL(B.c_key[1], C); AL(B.rec, 3 * C); AL(B.c_delta, C);
     AL(B.lamA[0], C); AL(B.lamA[1], C); AL(B.lamB[0], C); AL(B.lamB[1], C);
     AL(B.lamW[0], 2 * C); AL(B.lamW[1], 2 * C); AL(B.inc, 2 * C);
-    AL(B.c_self, C); AL(B.c_pos, C); AL(B.imp, 2 * C);
+    AL(B.c_self, C); AL(B.c_pos, C); AL(B.c_idx, C); AL(B.imp, 2 * C);
     AL(B.g_key[0], GC); AL(B.g_key[1], GC); AL(B.grec, 6 * GC); AL(B.g_delta, GC);
     AL(B.glamA[0], GC); AL(B.glamA[1], GC); AL(B.glamB[0], GC); AL(B.glamB[1], GC);
     AL(B.glamW[0], 2 * GC); AL(B.glamW[1], 2 * GC); AL(B.g_body, GC); AL(B.gsh, GC);
@@ -577,6 +588,8 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     CK(cudaMemsetAsync(B.geo_start[1], 0, (N + 1) * sizeof(int), s));
     CK(cudaMemsetAsync(B.inc_start, 0, (N + 1) * sizeof(int), s));
     CK(cudaMemsetAsync(B.err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(B.committed, 0, sizeof(long long), s));
+    CK(cudaMemsetAsync(B.need, 0, 2 * sizeof(int), s));
     CK(cudaMemsetAsync(B.resorted, 0, sizeof(int), s));
     CK(cudaMemsetAsync(B.gacc, 0, 6 * std::max(P.ng, 1) * sizeof(long long), s));
     CK(cudaMemsetAsync(B.grp, 0, DEM_MAX_GROUPS * sizeof(GroupDev), s));
@@ -659,8 +672,9 @@ static int body_pre(dem_bed* b, int p) {
     k += launch_scan(B.cell_cnt, B.cell_start, P.n_cells, B.scan_tmp, s);
     k += launch_cell_fill(P, B, s);
     k += launch_pairs(P, B, s);
+    // after a fault the scan keeps the last committed step's lists (its warm start)
     k += launch_scan3(B.own_cnt, B.own_cnt, B.in_cnt, B.geo_cnt, B.own_start[p], B.inc_start,
-                      B.geo_start[p], P.n, B.scan_tmp, s);
+                      B.geo_start[p], P.n, B.scan_tmp, s, B.err);
     k += launch_contacts_build(P, B, p, s);
     k += launch_inc_sort(P, B, s);
     if (P.v_imp > 0.f && b->imp.row) {
@@ -769,20 +783,32 @@ static void collect_timing(dem_bed* b) {
     b->ev_used.clear();
 }
 
+static dem_status grow_and_replay(dem_bed* b);
+
+// Synchronise and report a latched device fault.  A contact-storage overflow
+// is repaired: the arrays grow and the steps from the last committed one are
+// run again (grow_and_replay); other faults latch the bed.
 static dem_status check_fault(dem_bed* b) {
-    int err = 0;
-    CK(cudaMemcpyAsync(&err, b->B.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
-    CK(cudaStreamSynchronize(b->stream));
-    if (b->timing) collect_timing(b);
-    if (err) {
+    for (int round = 0;; ++round) {
+        int err = 0;
+        CK(cudaMemcpyAsync(&err, b->B.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        if (b->timing) collect_timing(b);
+        if (!err) return DEM_OK;
+        if (err == DEM_FLAG_CAPACITY && !b->no_grow && round < 8) {
+            const dem_status st = grow_and_replay(b);
+            if (st == DEM_OK) continue;
+            if (st != DEM_ERR_CAPACITY) {
+                b->faulted = true;
+                return st;
+            }
+        }
         b->faulted = true;
         if (err & DEM_FLAG_TIMEOUT) return fail(DEM_ERR_TIMEOUT, "a bounded wait of the resident sweep gave up");
-        if (err & DEM_FLAG_CAPACITY)
-            return fail(DEM_ERR_CAPACITY, "contact storage overflowed (capacity %d contacts, %d per body)",
-                        b->P.max_contacts, DEM_MAX_OWN);
-        return fail(DEM_ERR_NONFINITE, "non-finite velocity");
+        if (err & DEM_FLAG_NONFINITE) return fail(DEM_ERR_NONFINITE, "non-finite velocity");
+        return fail(DEM_ERR_CAPACITY, "contact storage overflowed (capacity %d contacts, %d per body)",
+                    b->P.max_contacts, b->P.max_own);
     }
-    return DEM_OK;
 }
 
 dem_status dem_check_fault(dem_bed* b) { return check_fault(b); }
@@ -846,8 +872,16 @@ static dem_status pgs_solve(dem_bed* b, int p) {
     return DEM_OK;
 }
 
+// a re-sort is due before this step (unless it already ran in the step that
+// overflowed and is being re-run)
+static bool resort_due(dem_bed* b) {
+    const bool due = b->g_resort && b->steps % b->resort_every == 0 && !b->skip_resort;
+    b->skip_resort = false;
+    return due;
+}
+
 dem_status dem_launch_step(dem_bed* b) {
-    const bool resort = b->g_resort && b->steps % b->resort_every == 0;
+    const bool resort = resort_due(b);
     const int p = (int)(b->steps & 1);
     if (resort) CK(cudaGraphLaunch(b->g_resort, b->stream));
     CK(cudaGraphLaunch(b->g[p][0], b->stream));
@@ -867,9 +901,9 @@ extern "C" dem_status dem_step(dem_bed* b, int32_t nsteps) {
     if (b->faulted) return fail(DEM_ERR_STATE, "the bed holds a latched device fault");
     CK(cudaSetDevice(b->dev));
     for (int k = 0; k < nsteps; ++k) {
-        const bool resort = b->g_resort && b->steps % b->resort_every == 0;
-        const int p = (int)(b->steps & 1);
         if (b->timing) {
+            const bool resort = resort_due(b);
+            const int p = (int)(b->steps & 1);
             if (b->ev_used.size() >= 4096) {
                 CK(cudaStreamSynchronize(b->stream));
                 collect_timing(b);
@@ -891,6 +925,116 @@ extern "C" dem_status dem_step(dem_bed* b, int32_t nsteps) {
             if (st != DEM_OK) return st;
         }
     }
+    return DEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// contact-capacity growth
+// ---------------------------------------------------------------------------
+// A new allocation of `bytes` in place of *p, keeping its first `keep` bytes.
+static dem_status regrow(dem_bed* b, void** p, size_t bytes, size_t keep) {
+    void* q = nullptr;
+    dem_status st = dalloc(b, &q, bytes);
+    if (st != DEM_OK) return st;
+    if (keep && *p) CK(cudaMemcpyAsync(q, *p, keep, cudaMemcpyDeviceToDevice, b->stream));
+    if (*p) dem_dfree(b, *p);
+    *p = q;
+    return DEM_OK;
+}
+
+// Buffers created on first use at the old capacity: freed, made again when used.
+static void drop_capacity_buffers(dem_bed* b) {
+    auto fr = [&](void* p) { if (p) dem_dfree(b, p); };
+    ImpBuf& I = b->imp;
+    fr(I.row); fr(I.tgt); fr(I.p[0]); fr(I.p[1]); fr(I.grow); fr(I.glev); fr(I.gtgt); fr(I.gp[0]); fr(I.gp[1]);
+    fr(I.bed); fr(I.count);
+    b->imp = ImpBuf{};
+    PgsBuf& S = b->pgs;
+    fr(S.col); fr(S.prio); fr(S.key); fr(S.gbody); fr(S.list); fr(S.remaining); fr(S.ncol); fr(S.colcnt);
+    fr(S.colstart); fr(S.colfill);
+    b->pgs = PgsBuf{};
+    b->pgs_cap = 0;
+    dem_adjoint_drop(b);
+}
+
+// New capacities: C sphere-sphere and G sphere-geometry contacts, own / geob
+// per body.  The warm-start lists of both parities (keys, world-frame impulses,
+// overlaps) are carried over; every other contact array is rebuilt by the next step.
+static dem_status grow_capacity(dem_bed* b, int64_t C, int64_t G, int own, int geob) {
+    SimParams& P = b->P;
+    DevBuf& B = b->B;
+    const size_t N = std::max(P.n, 1), C0 = P.max_contacts, G0 = P.max_geo;
+    dem_status st = DEM_OK;
+#define RE(ptr, cnt, keep) \
+    if (st == DEM_OK) st = regrow(b, (void**)&(ptr), (size_t)(cnt) * sizeof(*(ptr)), (size_t)(keep) * sizeof(*(ptr)))
+    if ((size_t)C != C0) {
+        RE(B.c_other, C, 0); RE(B.c_key[0], C, C0); RE(B.c_key[1], C, C0); RE(B.rec, 3 * C, 0);
+        RE(B.c_delta, C, C0); RE(B.lamA[0], C, 0); RE(B.lamA[1], C, 0); RE(B.lamB[0], C, 0); RE(B.lamB[1], C, 0);
+        RE(B.lamW[0], 2 * C, 2 * C0); RE(B.lamW[1], 2 * C, 2 * C0); RE(B.inc, 2 * C, 0); RE(B.c_self, C, 0);
+        RE(B.c_pos, C, 0); RE(B.c_idx, C, 0); RE(B.imp, 2 * C, 0);
+    }
+    if ((size_t)G != G0) {
+        RE(B.g_key[0], G, G0); RE(B.g_key[1], G, G0); RE(B.grec, 6 * G, 0); RE(B.g_delta, G, G0);
+        RE(B.glamA[0], G, 0); RE(B.glamA[1], G, 0); RE(B.glamB[0], G, 0); RE(B.glamB[1], G, 0);
+        RE(B.glamW[0], 2 * G, 2 * G0); RE(B.glamW[1], 2 * G, 2 * G0); RE(B.g_body, G, 0); RE(B.gsh, G, 0);
+        RE(B.gl_list, G, 0);
+    }
+    if (own != P.max_own) RE(B.tmp_own, N * own, 0);
+    if (geob != P.max_geo_body) RE(B.tmp_geo, N * geob, 0);
+#undef RE
+    if (st != DEM_OK) return st;
+    P.max_contacts = (int)C;
+    P.max_geo = (int)G;
+    P.max_own = own;
+    P.max_geo_body = geob;
+    drop_capacity_buffers(b);
+    return rebuild_graphs(b);
+}
+
+// After a contact-storage overflow: the step that overflowed and the steps
+// enqueued after it did not change the bed (kernels skip their writes while
+// the fault flag is set).  Read what the overflow needed, grow the arrays,
+// clear the flag and enqueue those steps again from the last committed one.
+// Host commands issued between them (plate velocities, loads) have already
+// taken their latest values, which the re-run steps use.
+static dem_status grow_and_replay(dem_bed* b) {
+    const SimParams& P = b->P;
+    const DevBuf& B = b->B;
+    cudaStream_t s = b->stream;
+    long long committed = 0;
+    int need[2] = {0, 0}, resorted = 0, tot[2] = {0, 0};
+    CK(cudaMemcpyAsync(&committed, B.committed, sizeof committed, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(need, B.need, sizeof need, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&resorted, B.resorted, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // totals of the step that overflowed (its scan ran when the overflow came
+    // after it; otherwise these are an older committed step's, within capacity)
+    const int pf = (int)(committed & 1);
+    if (P.n > 0) {
+        CK(cudaMemcpyAsync(&tot[0], B.own_start[pf] + P.n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&tot[1], B.geo_start[pf] + P.n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    if (committed > b->steps) return fail(DEM_ERR_STATE, "committed step count ahead of the enqueued steps");
+    auto grown = [](int64_t need, int64_t have, int64_t pad) {
+        return need > have ? std::max(have, need + need / 4 + pad) : have;
+    };
+    const int64_t C = grown(tot[0], P.max_contacts, 1024), G = grown(tot[1], P.max_geo, 1024);
+    const int64_t own = grown(need[0], P.max_own, 8), geob = grown(need[1], P.max_geo_body, 4);
+    if (C == P.max_contacts && G == P.max_geo && own == P.max_own && geob == P.max_geo_body)
+        return fail(DEM_ERR_CAPACITY, "contact storage overflowed and no limit could be raised");
+    if (C > 0x3fffffff || G > 0x3fffffff || own > 4096 || geob > 4096 ||
+        (int64_t)std::max(P.n, 1) * std::max(own, geob) > (int64_t)0x7fffffff)
+        return fail(DEM_ERR_CAPACITY, "contact storage overflowed beyond the largest supported capacity");
+    dem_status st = grow_capacity(b, C, G, (int)own, (int)geob);
+    if (st != DEM_OK) return st;
+    CK(cudaMemsetAsync(B.err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(B.need, 0, 2 * sizeof(int), s));
+    const int64_t target = b->steps;
+    b->steps = committed;
+    b->skip_resort = resorted != 0;
+    b->grows++;
+    for (int64_t k = committed; k < target; ++k)
+        if ((st = dem_launch_step(b)) != DEM_OK) return st;
     return DEM_OK;
 }
 
@@ -996,10 +1140,14 @@ extern "C" dem_status dem_read_forces(dem_bed* b, int32_t g, double f[3], double
     CK(cudaSetDevice(b->dev));
     long long acc[6];
     GeomDev G;
-    CK(cudaMemcpyAsync(acc, b->B.gacc + 6 * g, sizeof acc, cudaMemcpyDeviceToHost, b->stream));
-    CK(cudaMemcpyAsync(&G, b->B.geom + g, sizeof G, cudaMemcpyDeviceToHost, b->stream));
-    dem_status st = check_fault(b);
-    if (st != DEM_OK) return st;
+    for (;;) {   // again if the check re-ran overflowed steps
+        const int grows = b->grows;
+        CK(cudaMemcpyAsync(acc, b->B.gacc + 6 * g, sizeof acc, cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaMemcpyAsync(&G, b->B.geom + g, sizeof G, cudaMemcpyDeviceToHost, b->stream));
+        dem_status st = check_fault(b);
+        if (st != DEM_OK) return st;
+        if (b->grows == grows) break;
+    }
     const double sc = 1.0 / (DEM_FIX_SCALE * (double)b->P.dt);
     for (int k = 0; k < 3; ++k) {
         if (f) f[k] = (double)acc[k] * sc;
@@ -1045,11 +1193,16 @@ extern "C" dem_status dem_read_state(dem_bed* b, double* pos, float* vel, float*
     std::vector<VW> hv(n);
     std::vector<int> hid(n);
     cudaStream_t s = b->stream;
-    CK(cudaMemcpyAsync(hp.data(), b->B.pos, n * sizeof(double4_32a), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hv.data(), b->B.vw0, n * sizeof(VW), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hid.data(), b->B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s));
-    dem_status st = check_fault(b);
-    if (st != DEM_OK) return st;
+    dem_status st;
+    for (;;) {   // again if the check re-ran overflowed steps
+        const int grows = b->grows;
+        CK(cudaMemcpyAsync(hp.data(), b->B.pos, n * sizeof(double4_32a), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hv.data(), b->B.vw0, n * sizeof(VW), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hid.data(), b->B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+        st = check_fault(b);
+        if (st != DEM_OK) return st;
+        if (b->grows == grows) break;
+    }
     std::vector<double> op(3 * (size_t)n);
     std::vector<float> ov(3 * (size_t)n), ow(3 * (size_t)n);
     for (int i = 0; i < n; ++i) {
@@ -1072,7 +1225,9 @@ extern "C" dem_status dem_read_contacts(dem_bed* b, int64_t cap, int32_t* key_a,
     CK(cudaSetDevice(b->dev));
     *count = 0;
     const int n = b->P.n;
-    if (b->steps == 0 || n == 0) return check_fault(b);
+    // repair a pending overflow first (it re-runs steps), then read
+    dem_status st0 = check_fault(b);
+    if (st0 != DEM_OK || b->steps == 0 || n == 0) return st0;
     const int p = (int)((b->steps - 1) & 1);   // parity of the last step
     cudaStream_t s = b->stream;
     const DevBuf& B = b->B;
@@ -1137,6 +1292,10 @@ extern "C" dem_status dem_get_info(dem_bed* b, dem_info* out) {
     g_err.clear();
     if (!b || !out) return fail(DEM_ERR_ARG, "NULL argument");
     CK(cudaSetDevice(b->dev));
+    {   // repair a pending overflow first (it re-runs steps and grows arrays), then read
+        const dem_status st = check_fault(b);
+        if (st != DEM_OK) return st;
+    }
     memset(out, 0, sizeof *out);
     out->n = b->P.n;
     out->n_levels = b->P.n_levels;

@@ -51,6 +51,11 @@ struct dem_bed {
     // Newton impact stage buffers, created when the stage is first enabled
     ImpBuf imp{};
     int capture_err = 0;        // CUDA error of a graph call made while capturing (0: none)
+    // contact-capacity growth: after an overflow the steps from the last
+    // committed one are re-run with larger arrays
+    bool skip_resort = false;   // the next step's re-sort already ran (in the step that overflowed)
+    bool no_grow = false;       // set while a differentiation window is recorded
+    int grows = 0;              // capacity growths so far
     cudaStream_t side = nullptr;   // captures the bodies of conditional graph nodes
 };
 
@@ -68,6 +73,9 @@ dem_status dem_launch_step(dem_bed* b);
 void dem_set_error_message(const char* msg);
 // free the differentiation state (adjoint.cu)
 void dem_adjoint_release(dem_bed* b);
+// free the differentiation state and every device buffer it holds (sized by
+// the contact capacity, which is about to change)
+void dem_adjoint_drop(dem_bed* b);
 
 #define DEM_CK(call)                                                                          \
     do {                                                                                      \

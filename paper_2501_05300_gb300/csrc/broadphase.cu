@@ -21,6 +21,17 @@
 // arithmetic, against tol = 10 2^-24 of the coordinates + 80 2^-24 r_max; so an
 // accepted pair's double distance is below r_a + r_b by far more than the
 // double predicate's rounding.  The contact set is the exact predicate's.
+//
+// tol follows the particles: every step it is recomputed from that step's
+// largest |coordinate| (the per-level boxes of k_cell_count), so the bound holds
+// however far particles travel from where they were created.  It never drops
+// below the creation-time tolerance the cells were sized with.  Growing it keeps
+// the 27-cell search complete: inside a level's grid a coordinate is at most its
+// creation extent plus the margin, where the cells' 2 tol of slack covers the
+// FP32 rounding of the cell coordinates; outside it coordinates are clamped to
+// the boundary cells, which only brings two particles' cells closer.  Primitives
+// take their own tolerance, from the particles' and the primitives' coordinates
+// (an FP32 plane test rounds both).
 #include "dem_internal.cuh"
 
 #define BP_T 128
@@ -79,7 +90,36 @@ __global__ void __launch_bounds__(BP_T) k_cell_count(SimParams P, DevBuf B) {
     }
 }
 
+// FP32 tolerance bounding the error of an FP32 distance between points whose
+// coordinates are at most a in magnitude, for radii up to rmax (see the header)
+static __device__ __forceinline__ float fp32_tol(float a, float rmax) {
+    return 4.0f * ldexpf(1.25f * a + 8.0f * rmax, -23) + 8.0f * ldexpf(2.0f * rmax, -24);
+}
+
 __global__ void __launch_bounds__(BP_T) k_cell_fill(SimParams P, DevBuf B) {
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        // this step's tolerances, from the boxes k_cell_count has just built
+        // (an empty level keeps lo > hi)
+        float a = 0.0f, rmax = 0.0f;
+        for (int t = threadIdx.x; t < 3 * P.n_levels; t += 32) {
+            const int lo = B.lvl_lo[t], hi = B.lvl_hi[t];
+            if (lo <= hi) a = fmaxf(a, fmaxf(fabsf(ord_float(lo)), fabsf(ord_float(hi))));
+        }
+        for (int l = threadIdx.x; l < P.n_levels; l += 32) rmax = fmaxf(rmax, B.lv[l].rmax);
+        float ag = a;
+        for (int g = threadIdx.x; g < P.ng; g += 32)
+            ag = fmaxf(ag, fmaxf(fabsf(B.geom[g].fc[0]), fmaxf(fabsf(B.geom[g].fc[1]), fabsf(B.geom[g].fc[2]))));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+            ag = fmaxf(ag, __shfl_xor_sync(0xffffffffu, ag, o));
+            rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        }
+        if (threadIdx.x == 0) {
+            B.tolv[0] = fmaxf(P.tol, fp32_tol(a, rmax));
+            B.tolv[1] = fmaxf(P.tol, fp32_tol(ag, rmax));
+        }
+    }
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     int c = B.body_cell[i];
@@ -98,15 +138,16 @@ __global__ void __launch_bounds__(BP_T) k_cell_fill(SimParams P, DevBuf B) {
 __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gt / PT, lane = gt % PT;
-    if (i >= P.n) return;   // whole groups leave together
+    if (i >= P.n || *B.err) return;   // whole groups leave together
     const int grp = (threadIdx.x & 31) / PT;
     const unsigned gmask = 0xffu << (grp * PT);
     const unsigned below = (1u << lane) - 1u;
     const float4 pi = B.posr[i];
     const double4_32a xi = B.pos[i];
+    const float tol = B.tolv[0], tol_g = B.tolv[1];
     const int li = B.lvl[i];
     const int idi = B.id[i];
-    int2* own = B.tmp_own + (size_t)i * DEM_MAX_OWN;
+    int2* own = B.tmp_own + (size_t)i * P.max_own;
     int nown = 0;
     bool overflow = false;
     const int lend = B.lv[li].lend, gbeg = B.lv[li].g0, gend = B.lv[li].g1;
@@ -114,7 +155,7 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
         const LevelGrid g = B.lv[l];
         if (l > li) {
             // skip a coarser level whose particles are all out of reach
-            const float reach = pi.w + g.rmax + P.tol;
+            const float reach = pi.w + g.rmax + tol;
             const float q[3] = {pi.x, pi.y, pi.z};
             bool far = false;
 #pragma unroll
@@ -152,7 +193,7 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
                 for (int r = 1; r < 9; ++r)
                     if (t >= pre[r]) k = st[r] + (t - pre[r]);
                 const float4 pj = B.cell_pos[k];
-                const float R = pi.w + pj.w + P.tol;
+                const float R = pi.w + pj.w + tol;
                 const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
                 const float d2 = dx * dx + dy * dy + dz * dz;
                 if (d2 < R * R) {
@@ -163,7 +204,7 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
                         if (!(l == li && idj < idi)) {
                             // FP32 accept (see the header); only the band around
                             // contact takes the FP64 test
-                            const float Rin = fmaxf(pi.w + pj.w - P.tol, 0.0f);
+                            const float Rin = fmaxf(pi.w + pj.w - tol, 0.0f);
                             hit = d2 < Rin * Rin || exact_pair(xi, B.pos[j]);
                         }
                     }
@@ -172,7 +213,7 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
             const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & 0xffu;
             if (hit) {
                 const int q = nown + __popc(bal & below);
-                if (q < DEM_MAX_OWN) {
+                if (q < P.max_own) {
                     own[q] = make_int2(j, idj);
                     atomicAdd(&B.in_cnt[j], 1);
                 } else {
@@ -183,26 +224,29 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
         }
     }
     int ngeo = 0;
-    int* gl = B.tmp_geo + (size_t)i * DEM_MAX_GEO;
+    int* gl = B.tmp_geo + (size_t)i * P.max_geo_body;
     for (int base = gbeg; base < gend; base += PT) {
         const int gi = base + lane;
         bool hit = false;
         if (gi < gend) {
             const GeomDev& g = B.geom[gi];
-            hit = geom_near(g, pi, P.tol) && geom_hit(g, xi.x, xi.y, xi.z, xi.w).hit;
+            hit = geom_near(g, pi, tol_g) && geom_hit(g, xi.x, xi.y, xi.z, xi.w).hit;
         }
         const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & 0xffu;
         if (hit) {
             const int q = ngeo + __popc(bal & below);
-            if (q < DEM_MAX_GEO) gl[q] = gi;
+            if (q < P.max_geo_body) gl[q] = gi;
             else overflow = true;
         }
         ngeo += __popc(bal);
     }
     __syncwarp(gmask);
     if (lane == 0) {
-        nown = min(nown, DEM_MAX_OWN);
-        ngeo = min(ngeo, DEM_MAX_GEO);
+        // an overflow records the size that would have held this body's lists
+        if (nown > P.max_own) atomicMax(&B.need[0], nown);
+        if (ngeo > P.max_geo_body) atomicMax(&B.need[1], ngeo);
+        nown = min(nown, P.max_own);
+        ngeo = min(ngeo, P.max_geo_body);
         // order the list by the other particle's stable id (primitives by index)
         for (int a = 1; a < nown; ++a) {
             const int2 v = own[a];
@@ -225,11 +269,11 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
 // Owned lists -> contact arrays; both ends of every contact -> incidence lists.
 __global__ void __launch_bounds__(BP_T) k_contacts_build(SimParams P, DevBuf B, int parity) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+    if (i >= P.n || *B.err) return;
     const int os = B.own_start[parity][i];
     const int no = B.own_cnt[i];
     const int is = B.inc_start[i];
-    const int2* own = B.tmp_own + (size_t)i * DEM_MAX_OWN;
+    const int2* own = B.tmp_own + (size_t)i * P.max_own;
     const long long inc_cap = 2LL * P.max_contacts;
     for (int k = 0; k < no; ++k) {
         const int c = os + k;
@@ -246,7 +290,7 @@ __global__ void __launch_bounds__(BP_T) k_contacts_build(SimParams P, DevBuf B, 
     }
     const int gs = B.geo_start[parity][i];
     const int ng = B.geo_cnt[i];
-    const int* gl = B.tmp_geo + (size_t)i * DEM_MAX_GEO;
+    const int* gl = B.tmp_geo + (size_t)i * P.max_geo_body;
     const int gcap = P.max_geo;
     for (int k = 0; k < ng; ++k) {
         if (gs + k >= gcap) { set_flag(B.err, DEM_FLAG_CAPACITY); break; }
@@ -296,8 +340,14 @@ __global__ void __launch_bounds__(BP_T) k_inc_sort(SimParams P, DevBuf B) {
     for (int k = 0; k < m; ++k) {
         const int2 v = L[k];
         const int c = v.x & 0x7fffffff;
-        if (v.x < 0) B.c_pos[c].y = s + k;
-        else B.c_pos[c].x = s + k;
+        if (v.x < 0) {          // b's entry: the other body is the owner a
+            B.c_pos[c].y = s + k;
+            B.c_idx[c].w = s + k;
+        } else {                // the owner's entry: the other body is b
+            B.c_pos[c].x = s + k;
+            *reinterpret_cast<int2*>(&B.c_idx[c]) = make_int2(i, v.y);
+            B.c_idx[c].z = s + k;
+        }
     }
 }
 

@@ -21,8 +21,8 @@
 
 #define DEM_MAX_LEVELS 256  // grid levels over all beds (radius bands x beds)
 #define DEM_MAX_GEOM 512    // kinematic primitives over all beds
-#define DEM_MAX_OWN 32   // sphere-sphere contacts one body may own per step
-#define DEM_MAX_GEO 8    // sphere-geometry contacts per body per step
+#define DEM_MAX_OWN 32   // sphere-sphere contacts one body may own per step (initial; grows on overflow)
+#define DEM_MAX_GEO 8    // sphere-geometry contacts per body per step (initial; grows on overflow)
 #define DEM_FIX_SCALE 17592186044416.0  // 2^44: fixed-point scale of geometry impulses [N s]
 #define DEM_MAX_GROUPS 16  // load-driven rigid groups of primitives
 
@@ -86,6 +86,8 @@ struct SimParams {
     int n, ng, n_levels, n_it;
     int max_contacts;   // capacity of the sphere-sphere contact arrays
     int max_geo;        // capacity of the sphere-geometry contact arrays
+    int max_own;        // sphere-sphere contacts one body may own per step
+    int max_geo_body;   // sphere-geometry contacts of one body per step
     int n_cells;
     float dt, inv_dt;
     float e_H, kn_scale, eps_reg, delta_floor;
@@ -93,7 +95,8 @@ struct SimParams {
     float Estar_ss;     // particle-particle effective modulus
     float mu_t, mu_r;
     float gx, gy, gz;
-    float tol;          // FP32 broad-phase tolerance [m], covers FP32 rounding of positions
+    float tol;          // FP32 narrow-phase tolerance [m] at creation: the cells are sized with it,
+                        //   and each step's tolerance (tolv) is never below it
     int lanes;          // sweep layout: 0 two-pass, else threads per body in one kernel
     int nit_uniform;    // 1 when every bed takes n_it sweeps
     int n_groups;       // load-driven groups
@@ -101,7 +104,14 @@ struct SimParams {
     float e_imp;        // Newton impact stage: restitution coefficient
     float v_imp;        // impact threshold [m/s]; 0: no impact stage
     int n_beds;
+    unsigned spin_limit;   // polls of one neighbour counter before a resident-sweep wait gives up
 };
+
+// Polls of one neighbour counter before a wait of the resident sweep gives up
+// (about a second).  The environment variable DEM_TEST_SPIN_LIMIT, read when a
+// bed is created, overrides it: a test knob that makes the waits give up at
+// once, to exercise the DEM_ERR_TIMEOUT path without a hung kernel.
+#define DEM_SPIN_LIMIT (1u << 22)
 
 // Device pointers of one bed.  The two warm-start generations (parity of the
 // step number) are indexed [0] / [1].
@@ -116,10 +126,16 @@ struct DevBuf {
     int* lvl;
     int* prev_of;       // old slot of each slot after a re-sort
     int* resorted;      // 1 during the step that follows a re-sort
-    int* err;           // latched DEM_FLAG_* bits
+    int* err;           // latched DEM_FLAG_* bits.  While it is set no kernel writes the state
+                        //   that carries across steps, so the bed stays as the last
+                        //   committed step left it (the step can be re-run after a grow)
+    long long* committed;   // [1] steps completed without a fault
+    int* need;          // [2] largest per-body counts seen in an overflow: owned contacts,
+                        //   geometry contacts
     // broad phase
     int* lvl_lo;        // [3 * n_levels] per-level bounding box of the centres,
     int* lvl_hi;        //   floats as order-preserving ints, rebuilt every step
+    float* tolv;        // [2] this step's FP32 narrow-phase tolerance: sphere pairs, primitives
     int* body_cell;
     int* cell_cnt;      // [n_cells + 1]
     int* cell_start;    // [n_cells + 1]
@@ -127,8 +143,8 @@ struct DevBuf {
     int* cell_body;     // [n] slot of the particle in each cell position
     float4* cell_pos;   // [n] its FP32 centre and radius, in cell order
     // per-body candidate lists of the current step
-    int2* tmp_own;      // [n * DEM_MAX_OWN] (other slot, other stable id)
-    int* tmp_geo;       // [n * DEM_MAX_GEO] primitive index
+    int2* tmp_own;      // [n * max_own] (other slot, other stable id)
+    int* tmp_geo;       // [n * max_geo_body] primitive index
     int* own_cnt;       // [n + 1]
     int* in_cnt;        // [n + 1]
     int* geo_cnt;       // [n + 1]
@@ -148,6 +164,7 @@ struct DevBuf {
     int2* inc;          // [2C]
     int* c_self;        // [C] slot of body a (the owner)
     int2* c_pos;        // [C] positions of the contact in a's and b's incidence lists
+    int4* c_idx;        // [C] (slot of a, slot of b, c_pos.x, c_pos.y): one load in the sweep
     Imp* imp;           // [2C] per incidence entry: impulse share of its body
     // sphere-geometry contacts (one-sided)
     int* g_key[2];      // [max_geo] primitive index, per parity
@@ -181,9 +198,10 @@ struct DevBuf {
 // launch wrappers (each returns the number of kernels it enqueued)
 // ----------------------------------------------------------------------------
 int launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s);
-// three exclusive scans at once; column b scans b + b2 element-wise
+// three exclusive scans at once; column b scans b + b2 element-wise; nothing
+// is written while *skip != 0 (skip may be NULL)
 int launch_scan3(const int* a, const int* b, const int* b2, const int* c, int* oa, int* ob, int* oc,
-                 int n, int* tmp, cudaStream_t s);
+                 int n, int* tmp, cudaStream_t s, const int* skip);
 int launch_cell_count(const SimParams& P, const DevBuf& B, cudaStream_t s);
 int launch_cell_fill(const SimParams& P, const DevBuf& B, cudaStream_t s);
 int launch_pairs(const SimParams& P, const DevBuf& B, cudaStream_t s);

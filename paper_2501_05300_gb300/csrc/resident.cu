@@ -39,7 +39,6 @@
 #define RS_T 1024                  // threads per block
 #define RS_SMEM (220 * 1024)       // dynamic shared memory per block [B]
 #define RS_MAX_BLOCKS 1024
-#define RS_SPIN_LIMIT (1u << 22)   // polls of one neighbour counter (seconds at most)
 #define RS_XWORDS (RS_SMEM / 24 / 32 + 1)   // bit mask over the shared share slots
 
 static __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -89,12 +88,13 @@ static __device__ __forceinline__ void get_share(const float* sh, bool local, in
 
 // wait until every neighbour's counter (cnt[q], q in the mask) reaches k;
 // false if a wait gave up (or another block latched a fault)
-static __device__ bool wait_neighbours(const unsigned* mask, const int* cnt, int G, int k, int* err, int* stop) {
+static __device__ bool wait_neighbours(const unsigned* mask, const int* cnt, int G, int k, int* err, int* stop,
+                                       unsigned limit) {
     for (int q = threadIdx.x; q < G; q += RS_T) {
         if (!(mask[q >> 5] >> (q & 31) & 1u)) continue;
         unsigned spins = 0;
         while (ld_acquire(&cnt[q]) < k) {
-            if (++spins > RS_SPIN_LIMIT) {
+            if (++spins > limit) {
                 set_flag(err, DEM_FLAG_TIMEOUT);
                 *stop = 1;
                 break;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(RS_T, 1) k_resident(SimParams P, DevBuf B, Res
     for (int it = 0; it < nit; ++it) {
         const int src = it & 1, dst = src ^ 1;
         const bool last = it == nit - 1;
-        if (it > 0 && !wait_neighbours(nbmask, bdone, G, it, B.err, &s_stop)) return;
+        if (it > 0 && !wait_neighbours(nbmask, bdone, G, it, B.err, &s_stop, P.spin_limit)) return;
         const VW* vin = B.vw[src];
         // contact phase: the block's own contacts, then its geometry contacts;
         // the next item's indices are fetched while this one is computed
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(RS_T, 1) k_resident(SimParams P, DevBuf B, Res
             put_share(sh, bin, icap, pos.y - ibase, B.imp + pos.y, L, A);
         }
         publish(cdone, b, it + 1);
-        if (!wait_neighbours(nbmask, cdone, G, it + 1, B.err, &s_stop)) return;
+        if (!wait_neighbours(nbmask, cdone, G, it + 1, B.err, &s_stop, P.spin_limit)) return;
         // the shares other blocks wrote for this block's bodies, into their shared slots
         const int mcap = min(ninc, icap);
 #pragma unroll 4

@@ -35,9 +35,11 @@ __global__ void __launch_bounds__(RS_T) k_morton(SimParams P, DevBuf B) {
     B.val_a[i] = i;
 }
 
+// After a fault (a step not committed) the particles keep their order, and
+// the old slots of the last re-sort stay available to the step's re-run.
 __global__ void __launch_bounds__(RS_T) k_permute_gather(SimParams P, DevBuf B) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+    if (i >= P.n || *B.err) return;
     const int o = B.val_a[i];
     B.t_pos[i] = B.pos[o];
     B.t_vw[i] = B.vw0[o];
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(RS_T) k_permute_gather(SimParams P, DevBuf B) 
 
 __global__ void __launch_bounds__(RS_T) k_permute_store(SimParams P, DevBuf B) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+    if (i >= P.n || *B.err) return;
     const double4_32a x = B.t_pos[i];
     B.pos[i] = x;
     B.posr[i] = make_float4((float)x.x, (float)x.y, (float)x.z, (float)x.w);

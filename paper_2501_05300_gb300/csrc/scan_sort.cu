@@ -19,10 +19,12 @@ struct ScanCols {
     const int* in[3];
     const int* in2[3];  // optional second input added element-wise (NULL = none)
     int* out[3];
+    const int* skip;    // optional: when *skip != 0 the scan writes nothing (NULL = always run)
 };
 
 template <int C>
 __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(ScanCols a, int n, int* sums, int nb) {
+    if (a.skip && *a.skip) return;
     __shared__ int sm[C][SCAN_TILE];
     __shared__ int wsum[C][SCAN_T / 32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(ScanCols a, int n, int* s
 // writes the grand total to out[c][n].
 template <int C>
 __global__ void __launch_bounds__(1024) k_scan_sums(ScanCols a, int n, int* sums, int nb) {
+    if (a.skip && *a.skip) return;
     __shared__ int wsum[32];
     __shared__ int carry;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -133,6 +136,7 @@ __global__ void __launch_bounds__(1024) k_scan_sums(ScanCols a, int n, int* sums
 
 template <int C>
 __global__ void __launch_bounds__(SCAN_T) k_scan_add(ScanCols a, int n, const int* sums, int nb) {
+    if (a.skip && *a.skip) return;
     const int base = blockIdx.x * SCAN_TILE;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -170,8 +174,9 @@ int launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s) {
 }
 
 int launch_scan3(const int* x, const int* y, const int* y2, const int* z, int* ox, int* oy, int* oz,
-                 int n, int* tmp, cudaStream_t s) {
+                 int n, int* tmp, cudaStream_t s, const int* skip) {
     ScanCols a{};
+    a.skip = skip;
     a.in[0] = x; a.in[1] = y; a.in[2] = z;
     a.in2[1] = y2;
     a.out[0] = ox; a.out[1] = oy; a.out[2] = oz;

@@ -200,6 +200,9 @@ static __device__ __forceinline__ float sub_sum(float v) {
     return v;
 }
 
+static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+static __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 template <int T, bool UPDATE>
 __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, int it) {
     if (*B.err) return;
@@ -344,7 +347,10 @@ __global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p
     if (small)
         for (int t = threadIdx.x; t < 6 * P.ng; t += blockDim.x)
             if (sacc[t] != 0) atomicAdd((unsigned long long*)&B.gacc[t], (unsigned long long)sacc[t]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // a faulted step is not committed: primitives, groups and the re-sort
+    // mapping stay as they were, so the step can be re-run
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ok) {
+        ++*B.committed;
         // load-driven groups: the solved velocity of the final iterate moves
         // the members along the dynamic axes
         for (int q = 0; q < P.n_groups; ++q) {
@@ -398,105 +404,188 @@ int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s
 // dependent launch: a pass may start while the previous one drains and waits
 // (griddepcontrol.wait) before reading what it produced.
 // ---------------------------------------------------------------------------
-static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-static __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
-// 12 resident blocks per SM (40 registers): the pass is latency-bound, more
-// warps in flight beat the few spilled bytes
-__global__ void __launch_bounds__(SV_T, 12) k_contact_pass(SimParams P, DevBuf B, int p, int it, int nact) {
-    pdl_wait();
-    pdl_trigger();
-    if (*B.err) return;
-    group_clear_ahead(P, B, it);
-    const int src = it & 1, dst = src ^ 1;
+// Both passes read what the step produced before its sweeps (the fault flag,
+// each contact's bodies and incidence positions, its rows, each body's
+// incidence range and start velocity) before waiting for the previous pass, so
+// those loads overlap that pass's tail; only the iterates (impulses,
+// velocities, shares) are read after the wait.  None of the sweep kernels
+// writes the fault flag, so reading it early sees the step's value.
+//
+// Launch shape and register budgets of the two passes, chosen by timing on
+// the 200k refined bed (GB300): the contact pass at 64 registers (8 blocks of
+// 128 threads per SM, a grid of 16 blocks per SM, the next contact's indices
+// and rows prefetched), the body pass at 80 registers over one resident wave
+// of 6 blocks per SM.  Tighter budgets spill and lose more than the extra
+// warps gain.
+#ifndef DEM_CP_BLOCKS_PER_SM
+#define DEM_CP_BLOCKS_PER_SM 16
+#endif
+#ifndef DEM_CP_MINB
+#define DEM_CP_MINB 8
+#endif
+#ifndef DEM_CP_PIPE
+#define DEM_CP_PIPE 1
+#endif
+#ifndef DEM_BP_GEO_NOINLINE
+#define DEM_BP_GEO_NOINLINE 0
+#endif
+#ifndef DEM_BP_BLOCKS_PER_SM
+#define DEM_BP_BLOCKS_PER_SM 6
+#endif
+#ifndef DEM_BP_MINB
+#define DEM_BP_MINB 6
+#endif
+__global__ void __launch_bounds__(SV_T, DEM_CP_MINB) k_contact_pass(SimParams P, DevBuf B, int p, int it, int nact) {
+    const int bad = *B.err;
     // contacts are stored in owner order: those of the active prefix come first
     const int nc = min(B.own_start[p][nact], P.max_contacts);
+    const int stride = gridDim.x * blockDim.x;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    bool have = c < nc;
+    int4 id = make_int4(0, 0, 0, 0);
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    if (have) {
+        id = B.c_idx[c];
+        r0 = B.rec[3 * (size_t)c];
+        r1 = B.rec[3 * (size_t)c + 1];
+        r2 = B.rec[3 * (size_t)c + 2];
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (bad) return;
+    group_clear_ahead(P, B, it);
+    const int src = it & 1, dst = src ^ 1;
     const VW* __restrict__ vin = B.vw[src];
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        const int a = B.c_self[c], b = B.c_other[c];
-        const int nit = body_nit(P, B, a);
-        if (it >= nit) continue;              // this bed has finished its sweeps
-        const bool last = it == nit - 1;
-        const int2 pos = B.c_pos[c];
-        const float4 r0 = B.rec[3 * (size_t)c], r1 = B.rec[3 * (size_t)c + 1], r2 = B.rec[3 * (size_t)c + 2];
-        // the previous iterate is dead after this read: stream it (evict first)
-        const float4 l0 = __ldcs(&B.lamA[src][c]);
-        const float2 l1 = __ldcs(&B.lamB[src][c]);
-        const VW A = vin[a], Bv = vin[b];
-        const float3 va = f3(A.v), wa = f3(A.w), vb = f3(Bv.v), wb = f3(Bv.w);
-        const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, va - vb, wa, wb, P.eps_reg);
-        const float3 n = f3(r0);
-        if (last) {
-            write_world(B.lamW[p], c, n, u);
-        } else {
-            B.lamA[dst][c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
-            B.lamB[dst][c] = make_float2(u.pr.y, u.pr.z);
+    while (have) {
+        const int nit = body_nit(P, B, id.x);
+        const bool run = it < nit;            // else this bed has finished its sweeps
+        float4 l0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 l1 = make_float2(0.f, 0.f);
+        VW A, Bv;
+        if (run) {
+            // the previous iterate is dead after this read: stream it (evict first)
+            l0 = __ldcs(&B.lamA[src][c]);
+            l1 = __ldcs(&B.lamB[src][c]);
+            A = vin[id.x];
+            Bv = vin[id.y];
         }
-        float3 La = make_float3(0.f, 0.f, 0.f), Aa = La, Lb = La, Ab = La;
-        add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
-        add_impulse(n, u.t1, u.t2, r2.y, u.pn, u.pt1, u.pt2, u.pr, true, Lb, Ab);
-        Imp ia, ib;
-        ia.a = make_float4(La.x, La.y, La.z, Aa.x);
-        ia.b = make_float4(Aa.y, Aa.z, 0.f, 0.f);
-        ib.a = make_float4(Lb.x, Lb.y, Lb.z, Ab.x);
-        ib.b = make_float4(Ab.y, Ab.z, 0.f, 0.f);
-        B.imp[pos.x] = ia;
-        B.imp[pos.y] = ib;
+#if DEM_CP_PIPE
+        // the next contact's indices and rows, fetched while this one's
+        // iterates are in flight
+        const int cn = c + stride;
+        const bool hn = cn < nc;
+        int4 idn = id;
+        float4 n0 = r0, n1 = r1, n2 = r2;
+        if (hn) {
+            idn = B.c_idx[cn];
+            n0 = B.rec[3 * (size_t)cn];
+            n1 = B.rec[3 * (size_t)cn + 1];
+            n2 = B.rec[3 * (size_t)cn + 2];
+        }
+#endif
+        if (run) {
+            const bool last = it == nit - 1;
+            const float3 va = f3(A.v), wa = f3(A.w), vb = f3(Bv.v), wb = f3(Bv.w);
+            const Upd u = contact_update(r0, r1, r2.x, r2.y, r2.z, r2.w, l0, l1, va - vb, wa, wb, P.eps_reg);
+            const float3 n = f3(r0);
+            if (last) {
+                write_world(B.lamW[p], c, n, u);
+            } else {
+                B.lamA[dst][c] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+                B.lamB[dst][c] = make_float2(u.pr.y, u.pr.z);
+            }
+            float3 La = make_float3(0.f, 0.f, 0.f), Aa = La, Lb = La, Ab = La;
+            add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
+            add_impulse(n, u.t1, u.t2, r2.y, u.pn, u.pt1, u.pt2, u.pr, true, Lb, Ab);
+            Imp ia, ib;
+            ia.a = make_float4(La.x, La.y, La.z, Aa.x);
+            ia.b = make_float4(Aa.y, Aa.z, 0.f, 0.f);
+            ib.a = make_float4(Lb.x, Lb.y, Lb.z, Ab.x);
+            ib.b = make_float4(Ab.y, Ab.z, 0.f, 0.f);
+            B.imp[id.z] = ia;
+            B.imp[id.w] = ib;
+        }
+#if DEM_CP_PIPE
+        c = cn;
+        have = hn;
+        id = idn;
+        r0 = n0; r1 = n1; r2 = n2;
+#else
+        c += stride;
+        have = c < nc;
+        if (have) {
+            id = B.c_idx[c];
+            r0 = B.rec[3 * (size_t)c];
+            r1 = B.rec[3 * (size_t)c + 1];
+            r2 = B.rec[3 * (size_t)c + 2];
+        }
+#endif
     }
 }
 
-// BT lanes per body: lane l adds the body's shares l, l+BT, ...; the lane sums
-// are combined by a fixed butterfly, so the result does not depend on timing.
-#define BT 1
-// 12 resident blocks per SM (40 registers): measured 2 % faster per sweep than
-// the unbounded 56-register build on the refined bed; 16 (32 registers) spills
-__global__ void __launch_bounds__(SV_T, 12) k_body_pass(SimParams P, DevBuf B, int p, int it, int nact) {
-    pdl_wait();
-    pdl_trigger();
-    if (*B.err) return;
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = gt / BT, lane = gt % BT;
-    const int nit = i < P.n ? body_nit(P, B, i) : 0;
-    const bool active = i < P.n && it < nit;
-    const bool last = it == nit - 1;
+// A body's sphere-geometry contacts at sweep it: updated from its iterate,
+// their impulses added to (accL, accA) in list order.  Few bodies touch a
+// primitive; out of line, this path does not set the register budget of the
+// body pass's common path.
+#if DEM_BP_GEO_NOINLINE
+static __device__ __noinline__
+#else
+static __device__ __forceinline__
+#endif
+void body_geom_contacts(const SimParams& P, const DevBuf& B, int p, int it, int i, int k0, int k1, bool last,
+                        float3& accL, float3& accA) {
     const int src = it & 1, dst = src ^ 1;
-    float3 accL = make_float3(0.f, 0.f, 0.f), accA = accL;
-    if (active) {
-        const int e1 = B.inc_start[i + 1];
-        for (int e = B.inc_start[i] + lane; e < e1; e += BT) {
-            // a share is read once, by its body
-            const float4 qa = __ldcs(&B.imp[e].a);
-            const float4 qb = __ldcs(&B.imp[e].b);
-            accL = accL + f3(qa);
-            accA = accA + make_float3(qa.w, qb.x, qb.y);
+    const VW me = B.vw[src][i];
+    const float3 vi = f3(me.v), wi = f3(me.w);
+    for (int k = k0; k < k1; ++k) {
+        const float4* r = B.grec + 6 * (size_t)k;
+        const float4 r0 = r[0], r2 = r[2];
+        const float3 n = f3(r0);
+        bool done;
+        const Upd u = geom_update(P, B, r, k, src, it, vi, wi, done);
+        if (done) {
+        } else if (last) {
+            write_world(B.glamW[p], k, n, u);
+        } else {
+            B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+            B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
         }
-        const int g1 = B.geo_start[p][i + 1];
-        int k = B.geo_start[p][i] + lane;
-        if (k < g1) {
-            const VW me = B.vw[src][i];
-            const float3 vi = f3(me.v), wi = f3(me.w);
-            for (; k < g1; k += BT) {
-                const float4* r = B.grec + 6 * (size_t)k;
-                const float4 r0 = r[0], r2 = r[2];
-                const float3 n = f3(r0);
-                bool done;
-                const Upd u = geom_update(P, B, r, k, src, it, vi, wi, done);
-                if (done) {
-                } else if (last) {
-                    write_world(B.glamW[p], k, n, u);
-                } else {
-                    B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
-                    B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
-                }
-                add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
-            }
-        }
+        add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, accL, accA);
     }
-    accL = make_float3(sub_sum<BT>(accL.x), sub_sum<BT>(accL.y), sub_sum<BT>(accL.z));
-    accA = make_float3(sub_sum<BT>(accA.x), sub_sum<BT>(accA.y), sub_sum<BT>(accA.z));
-    if (!active || lane != 0) return;
-    const VW s0 = B.vw0[i];
-    const float4 v0 = s0.v, w0 = s0.w;
+}
+
+// The body pass loads a body's shares DEM_BP_CHUNK at a time, all before it
+// adds them, then adds them one by one in incidence order: the loads are in
+// flight together, the sum keeps its fixed order (and so its rounding).
+#ifndef DEM_BP_CHUNK
+#define DEM_BP_CHUNK 4
+#endif
+// One body's sum of its impulse shares in incidence order, its geometry
+// contacts, and v = v* + M^-1 sum.
+static __device__ __forceinline__ void body_update(const SimParams& P, const DevBuf& B, int p, int it, int i,
+                                                   int nit, int e0, int e1, int k0, int k1, float4 v0, float4 w0) {
+    const bool last = it == nit - 1;
+    const int dst = (it & 1) ^ 1;
+    float3 accL = make_float3(0.f, 0.f, 0.f), accA = accL;
+    for (int e = e0; e < e1; e += DEM_BP_CHUNK) {
+        // a share is read once, by its body: stream it
+        float4 qa[DEM_BP_CHUNK];
+        float2 qb[DEM_BP_CHUNK];
+#pragma unroll
+        for (int u = 0; u < DEM_BP_CHUNK; ++u)
+            if (e + u < e1) {
+                qa[u] = __ldcs(&B.imp[e + u].a);
+                qb[u] = __ldcs(reinterpret_cast<const float2*>(&B.imp[e + u].b));
+            }
+#pragma unroll
+        for (int u = 0; u < DEM_BP_CHUNK; ++u)
+            if (e + u < e1) {
+                accL = accL + f3(qa[u]);
+                accA = accA + make_float3(qa[u].w, qb[u].x, qb[u].y);
+            }
+    }
+    if (k0 < k1) body_geom_contacts(P, B, p, it, i, k0, k1, last, accL, accA);
     const float gm = v0.w > 0.0f ? P.dt : 0.0f;
     const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
     const float3 v = vs + v0.w * accL;
@@ -505,6 +594,46 @@ __global__ void __launch_bounds__(SV_T, 12) k_body_pass(SimParams P, DevBuf B, i
     out.v = make_float4(v.x, v.y, v.z, v0.w);
     out.w = make_float4(w.x, w.y, w.z, w0.w);
     B.vw[dst][i] = out;
+}
+
+__global__ void __launch_bounds__(SV_T, DEM_BP_MINB) k_body_pass(SimParams P, DevBuf B, int p, int it, int nact) {
+    const int bad = *B.err;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // the (first) body's incidence range and start velocity, before the wait
+    int nit = 0, e0 = 0, e1 = 0, k0 = 0, k1 = 0;
+    float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), w0 = v0;
+    if (i < nact) {
+        nit = body_nit(P, B, i);
+        e0 = B.inc_start[i];
+        e1 = B.inc_start[i + 1];
+        k0 = B.geo_start[p][i];
+        k1 = B.geo_start[p][i + 1];
+        v0 = B.vw0[i].v;
+        w0 = B.vw0[i].w;
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (bad) return;
+#if DEM_BP_BLOCKS_PER_SM > 0
+    // grid-stride over the bodies, the next body's range fetched ahead
+    const int stride = gridDim.x * blockDim.x;
+    for (; i < nact; i += stride) {
+        if (it < nit) body_update(P, B, p, it, i, nit, e0, e1, k0, k1, v0, w0);
+        const int j = i + stride;
+        if (j < nact) {
+            nit = body_nit(P, B, j);
+            e0 = B.inc_start[j];
+            e1 = B.inc_start[j + 1];
+            k0 = B.geo_start[p][j];
+            k1 = B.geo_start[p][j + 1];
+            v0 = B.vw0[j].v;
+            w0 = B.vw0[j].w;
+        }
+    }
+#else
+    // one body per thread (else this bed has finished its sweeps)
+    if (i < nact && it < nit) body_update(P, B, p, it, i, nit, e0, e1, k0, k1, v0, w0);
+#endif
 }
 
 // Contacts of load-driven groups at sweep it, one thread each: from the body's
@@ -771,8 +900,10 @@ int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int n
         return 1 + kg;
     }
     // two-pass sweep: contacts (grid-stride) then bodies
-    const int cblocks = std::max(1, std::min(nblk(nact * 8, SV_T), 16 * sm_count()));
-    const int bblocks = nblk(nact * BT, SV_T);
+    const int cblocks = std::max(1, std::min(nblk(nact * 8, SV_T), DEM_CP_BLOCKS_PER_SM * sm_count()));
+    // bodies: one per thread, or grid-stride over DEM_BP_BLOCKS_PER_SM blocks per SM
+    const int bblocks = DEM_BP_BLOCKS_PER_SM > 0 ? std::max(1, std::min(nblk(nact, SV_T), DEM_BP_BLOCKS_PER_SM * sm_count()))
+                                                 : nblk(nact, SV_T);
     launch_pdl(k_contact_pass, cblocks, s, P, B, parity, it, nact);
     const int kg = launch_group_contacts(P, B, parity, it, s);
     launch_pdl(k_body_pass, bblocks, s, P, B, parity, it, nact);

@@ -6,7 +6,7 @@ keeps its own grids, sweep count, primitives and warm starts."""
 import numpy as np
 import pytest
 
-from dem_cases import box_geoms, compressed_cloud, params
+from dem_cases import box_geoms, canonical_gpu_contacts, compressed_cloud, make_oracle, params
 from paper_2501_05300_gb300 import beds
 
 pytestmark = pytest.mark.gpu
@@ -75,3 +75,59 @@ def test_autotune_picks_a_valid_configuration():
     b.step(3)
     b.sync()
     b.close()
+
+
+def batch_bed_contacts(batch, k, specs):
+    """Bed k's contacts of the batch's last step in the bed's own numbering,
+    oriented like the oracle's (body a = lower stable id)."""
+    ab, bb, lb, db = batch.read_contacts()
+    o, m = batch.offsets[k], len(specs[k]["r"])
+    g0 = batch.geom_offsets[k]
+    sel = (ab >= o) & (ab < o + m)
+    a = ab[sel] - o
+    b = np.where(bb[sel] >= 0, bb[sel] - o, bb[sel] + g0)
+    return canonical_gpu_contacts(a, b, lb[sel])[:3]
+
+
+@pytest.mark.parametrize("lanes", [0, 2])
+def test_batch_beds_track_their_oracles(lanes):
+    """Every bed of a batch of three uneven beds (700 / 1500 / 3001 spheres,
+    N_it 20 / 35 / 50, a plate sinking into each) against its own FP64 oracle
+    run: contact sets bit-exact and impulses within 1e-5 after one step; after
+    15 steps (warm starts carried across two re-sorts) contact sets bit-exact,
+    velocities and displacements within 1e-4 and floor and plate forces within
+    1e-4."""
+    from paper_2501_05300_gb300.dem import Batch
+    specs = bed_list()
+    p = params()
+    p.pop("n_it")
+    batch = Batch(specs, resort_every=7, lanes=lanes, **p)
+    orcs = [make_oracle(s["x"], s["r"], params(n_it=s["n_it"]), s["geoms"]) for s in specs]
+    for steps in (1, 14):
+        batch.step(steps)
+        for o in orcs:
+            o.step(steps)
+        xb, vb, wb = batch.read_state()
+        for k, (s, o) in enumerate(zip(specs, orcs)):
+            a, b, lam = batch_bed_contacts(batch, k, specs)
+            oa, ob, olam, _, _ = o.contacts()
+            assert np.array_equal(a, oa) and np.array_equal(b, ob), (steps, k)
+            off, m = batch.offsets[k], len(s["r"])
+            xo, vo, wo = o.state()
+            if steps == 1:
+                scale = np.abs(olam).max()
+                assert np.abs(lam - olam).max() < 1e-5 * scale, k
+                assert np.abs(vb[off:off + m] - vo).max() < 1e-5 * np.abs(vo).max(), k
+            else:
+                assert np.abs(vb[off:off + m] - vo).max() < 1e-4 * np.abs(vo).max(), k
+                assert np.abs(wb[off:off + m] - wo).max() < 1e-4 * np.abs(wo).max(), k
+                disp = np.abs(xo - s["x"]).max()
+                assert np.abs(xb[off:off + m] - xo).max() < 1e-4 * disp, k
+                # the floor carries the bed; the plate may not have reached it yet
+                # (then both forces are exactly zero)
+                for gi in (0, len(s["geoms"]) - 1):
+                    fb, _, _ = batch.read_forces(batch.geom_offsets[k] + gi)
+                    fo, _ = o.geom_force(gi)
+                    assert gi != 0 or abs(fo[2]) > 0
+                    assert np.abs(fb - fo).max() <= 1e-4 * np.abs(fo).max(), (k, gi)
+    batch.close()

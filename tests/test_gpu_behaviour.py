@@ -68,19 +68,6 @@ def test_no_iterations_is_allowed():
     g.close()
 
 
-def test_capacity_overflow_is_reported_and_latched():
-    x, r = compressed_cloud(2000, seed=4)
-    g = make_gpu(x, r, params(n_it=5), contact_capacity=100)
-    g.step(1)
-    with pytest.raises(dem.DemError) as e:
-        g.sync()
-    assert e.value.status == dem.DEM_ERR_CAPACITY
-    with pytest.raises(dem.DemError) as e:
-        g.step(1)
-    assert e.value.status == dem.DEM_ERR_STATE
-    g.close()
-
-
 def test_invalid_arguments_are_rejected():
     x, r = compressed_cloud(10, seed=1)
     with pytest.raises(dem.DemError) as e:

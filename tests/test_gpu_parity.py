@@ -14,6 +14,7 @@ import pytest
 
 from dem_cases import (box_geoms, canonical_gpu_contacts, compressed_cloud, make_gpu, make_oracle,
                        params)
+import oracle
 from paper_2501_05300_gb300 import beds
 
 pytestmark = pytest.mark.gpu
@@ -187,4 +188,129 @@ def test_momentum_conserved_without_walls():
     # impulses are applied bit-identically at both ends; what remains is the
     # FP32 rounding of the velocity updates
     assert np.abs(P1 - P0).max() < 1e-5 * (m[:, None] * np.abs(vg)).sum()
+    g.close()
+
+
+def spinning_case(n, seed, n_it):
+    """The cloud with its primitives spinning: the floor turns about its
+    normal, the box paddle about the vertical through its centre while it
+    sinks, the cylinder tumbles about an oblique axis (its pose changes, so
+    detection follows the rotated primitive)."""
+    x, r, geoms, p = cloud_case(n, seed, n_it=n_it)
+    geoms[0].w = (0.0, 0.0, 2.0)
+    geoms[-2].w = (0.0, 0.0, 8.0)
+    geoms[-2].v = (0.0, 0.0, -0.02)
+    geoms[-1].w = (6.0, -3.0, 10.0)
+    return x, r, geoms, p
+
+
+def assert_poses_close(g, o, ng):
+    for k in range(ng):
+        pg, po = g.read_geom(k), o.geom(k)
+        assert np.abs(np.array(pg.R[:]) - np.array(po.R)).max() < 1e-12, k
+        assert np.abs(np.array(pg.c[:]) - np.array(po.c)).max() < 1e-14, k
+
+
+@pytest.mark.parametrize("n,seed", [(600, 41), (3001, 42)])
+def test_spinning_primitives_one_step(n, seed):
+    x, r, geoms, p = spinning_case(n, seed, n_it=60)
+    g = make_gpu(x, r, p, geoms)
+    o = make_oracle(x, r, p, geoms)
+    g.step(1)
+    o.step(1)
+    ok, (a, b, lam, dl), (oa, ob, olam, odl) = contact_sets_equal(g, o)
+    assert ok
+    assert {-1, -6, -7} <= set(np.unique(b[b < 0]).tolist())   # floor, paddle, cylinder touched
+    assert_impulses_close(lam, olam, 1e-5)
+    xg, vg, wg = g.read_state()
+    xo, vo, wo = o.state()
+    assert np.abs(vg - vo).max() < 1e-5 * np.abs(vo).max()
+    assert np.abs(wg - wo).max() < 1e-5 * np.abs(wo).max()
+    for k in (0, len(geoms) - 2, len(geoms) - 1):
+        fg, tg, _ = g.read_forces(k)
+        fo, to = o.geom_force(k)
+        assert np.abs(fg - fo).max() < 1e-5 * np.abs(fo).max(), k
+        assert np.abs(tg - to).max() < 1e-5 * np.abs(to).max(), k
+    assert_poses_close(g, o, len(geoms))
+    g.close()
+
+
+def test_spinning_primitives_200_steps():
+    x, r, geoms, p = spinning_case(1000, 43, n_it=50)
+    x0 = x.copy()
+    g = make_gpu(x, r, p, geoms, resort_every=9)
+    o = make_oracle(x, r, p, geoms)
+    for k in range(4):
+        g.step(50)
+        o.step(50)
+        xg, vg, wg = g.read_state()
+        xo, vo, wo = o.state()
+        assert np.abs(vg - vo).max() < 1e-4 * np.abs(vo).max(), k
+        assert np.abs(wg - wo).max() < 1e-4 * np.abs(wo).max(), k
+        assert np.abs(xg - xo).max() < 1e-4 * np.abs(xo - x0).max(), k
+        ok, _, _ = contact_sets_equal(g, o)
+        assert ok, k
+    gi = len(geoms) - 1
+    fg, tg, _ = g.read_forces(gi)
+    fo, to = o.geom_force(gi)
+    assert np.abs(fg - fo).max() < 1e-4 * np.abs(fo).max()
+    assert_poses_close(g, o, len(geoms))
+    g.close()
+
+
+def far_pairs(m, seed, gap):
+    """m isolated pairs on a lattice near the origin, each pair's centre
+    distance r_a + r_b + g with g uniform in [-gap, gap] along a random
+    direction: many pairs sit within a few FP32 ulps of touching once the
+    cloud is far from the origin."""
+    rng = np.random.default_rng(seed)
+    k = int(np.ceil(m ** 0.5))
+    r = rng.uniform(4e-3, 6e-3, 2 * m).astype(np.float32)
+    x = np.zeros((2 * m, 3))
+    for i in range(m):
+        base = np.array([(i % k) * 0.03, (i // k) * 0.03, 0.0])
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        d = float(r[2 * i]) + float(r[2 * i + 1]) + rng.uniform(-gap, gap)
+        x[2 * i] = base
+        x[2 * i + 1] = base + d * u
+    return x, r
+
+
+@pytest.mark.parametrize("vx", [6e6, -4e6])
+def test_contact_set_exact_far_from_origin(vx):
+    """A bed created near the origin and thrown 40-60 m along x in one step
+    (gravity off): the step's contact set there equals the exact predicate's
+    (FP64 brute force) on the positions it starts from, although at 40 m an
+    FP32 coordinate is rounded by up to 1.9e-6 m, far more than the tolerance
+    the bed was created with.  Pairs straddle contact within +-3 um."""
+    x, r = far_pairs(160, 51, 3e-6)
+    p = params(n_it=20, gravity=(0.0, 0.0, 0.0))
+    v = np.zeros((len(r), 3), np.float32)
+    v[:, 0] = vx
+    g = make_gpu(x, r, p, (), v=v)
+    g.step(1)
+    x1, _, _ = g.read_state()
+    assert np.abs(x1[:, 0]).min() > 35.0
+    g.step(1)
+    a, b, _, _ = g.read_contacts()
+    got = set(zip(np.minimum(a, b).tolist(), np.maximum(a, b).tolist()))
+    ea, eb, _ = oracle.detect(x1, r.astype(np.float64), np.arange(len(r), dtype=np.int32))
+    ref = set(zip(ea.tolist(), eb.tolist()))
+    assert got == ref
+    assert 40 < len(ref) < 150
+    # the case has teeth: with the creation-time tolerance, the FP32 accept or
+    # reject test misjudges some of these pairs at 40-60 m
+    absmax = np.abs(x).max()
+    rmax = float(r.max())
+    tol0 = 4 * 2.0 ** -23 * (1.25 * absmax + 8 * rmax) + 8 * 2.0 ** -24 * 2 * rmax
+    xf = x1.astype(np.float32)
+    i, j = np.arange(0, len(r), 2), np.arange(1, len(r), 2)
+    d = xf[i] - xf[j]
+    d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    R = r[i] + r[j]
+    accept = d2 < np.maximum(R - np.float32(tol0), 0) ** 2
+    reject = d2 >= (R + np.float32(tol0)) ** 2
+    exact = np.array([(int(p), int(q)) in ref for p, q in zip(i, j)])
+    assert (accept & ~exact).sum() + (reject & exact).sum() > 0
     g.close()

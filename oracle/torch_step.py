@@ -10,8 +10,11 @@ detection and is not differentiated; everything else is.
 The step is the same algorithm as oracle.c (Sec. 2.2 of the paper, SPOOK rows,
 N_it projected Jacobi sweeps with mass splitting, x += dt v), written with
 world-frame tangential vectors instead of a 2D tangent basis (the two agree:
-the tangential impulse always lies in the tangent plane).  Geometry is limited
-to planes.  Its forward values are pinned against oracle.c by the tests.
+the tangential impulse always lies in the tangent plane).  Geometry: planes,
+oriented boxes and cylinders that translate kinematically (no spin); the
+closest point takes the same cases as oracle.c (face, edge, corner, side,
+rim, centre inside), decided on the forward values and differentiated within
+the case.  Its forward values are pinned against oracle.c by the tests.
 """
 from __future__ import annotations
 
@@ -36,11 +39,63 @@ def _norm(a):
     return torch.where(pos, torch.sqrt(torch.where(pos, q, torch.ones_like(q))), torch.zeros_like(q))
 
 
+def _geom_contact(g, x, c, r):
+    """Unit normal (from the primitive to the sphere centre) and overlap of a
+    sphere of radius r at x with primitive g whose centre or reference point
+    is c; the case decisions of oracle.c's closest point, taken on the values,
+    the results differentiable in x and c."""
+    R = torch.tensor(g.R, dtype=torch.float64).reshape(3, 3)   # column k = local axis k
+    if g.type == _b.PLANE:
+        nz = R[:, 2]
+        return nz, r - _dot(nz, x - c)
+    q = R.T @ (x - c)
+    qd = q.detach().numpy()
+    if g.type == _b.BOX:
+        he = torch.tensor(g.he, dtype=torch.float64)
+        cl = torch.maximum(torch.minimum(q, he), -he)
+        e = q - cl
+        ee = float(_dot(e, e).detach())
+        if ee > 0.0:
+            d = torch.sqrt(_dot(e, e))
+            return R @ (e / d), r - d
+        depth = np.asarray(g.he) - np.abs(qd)
+        kb = int(np.argmin(depth))            # first minimum, as the C loop keeps
+        sg = -1.0 if qd[kb] < 0.0 else 1.0
+        nl = torch.zeros(3, dtype=torch.float64)
+        nl[kb] = sg
+        return R @ nl, r + (g.he[kb] - sg * q[kb])
+    Rc, H = g.he[0], g.he[2]
+    rho2 = q[0] * q[0] + q[1] * q[1]
+    if float(rho2.detach()) > Rc * Rc:
+        rho = torch.sqrt(rho2)
+        clxy = q[:2] * (Rc / rho)
+    else:
+        clxy = q[:2]
+    clz = torch.clamp(q[2], -H, H)
+    e = torch.cat([q[:2] - clxy, (q[2] - clz).reshape(1)])
+    ee = float(_dot(e, e).detach())
+    if ee > 0.0:
+        d = torch.sqrt(_dot(e, e))
+        return R @ (e / d), r - d
+    rho = torch.sqrt(rho2)
+    da = H - abs(qd[2])
+    dr = Rc - float(rho.detach())
+    if da <= dr:
+        sg = -1.0 if qd[2] < 0.0 else 1.0
+        return R @ torch.tensor([0.0, 0.0, sg], dtype=torch.float64), r + (H - sg * q[2])
+    if float(rho.detach()) > 0.0:
+        nl = torch.cat([q[:2] / rho, torch.zeros(1, dtype=torch.float64)])
+    else:
+        nl = torch.tensor([1.0, 0.0, 0.0], dtype=torch.float64)
+    return R @ nl, r + (Rc - rho)
+
+
 class TorchStepper:
     """params: OracleParams (dt, n_it, e_H, damp_steps, E, nu, rho, eps_reg,
     delta_floor, gravity); theta = (kn_scale, mu_t, mu_r) as torch tensors;
-    planes: list of oracle Geom of type PLANE (kinematic velocity allowed).
-    Particle-plane contacts use the plane's own mu_t, mu_r (not differentiated)."""
+    planes: list of oracle Geom (plane, box or cylinder; kinematic translation
+    allowed, no spin).  Particle-primitive contacts use the primitive's own
+    mu_t, mu_r (not differentiated)."""
 
     def __init__(self, params, r, ids, planes, inv_m=None, inv_I=None):
         self.p = params
@@ -96,10 +151,9 @@ class TorchStepper:
         n_g, delta_g, Estar_g, mut_g, mur_g, vg = [], [], [], [], [], []
         for k in range(ng_c):
             pl = self.planes[gg[k]]
-            nz = torch.tensor([pl.R[2], pl.R[5], pl.R[8]], dtype=torch.float64)
-            s = _dot(nz, x[ga[k]] - plane_pos[gg[k]])
-            n_g.append(nz)
-            delta_g.append(self.r[ga[k]] - s)
+            nk, dk = _geom_contact(pl, x[ga[k]], plane_pos[gg[k]], self.r[ga[k]])
+            n_g.append(nk)
+            delta_g.append(dk)
             Estar_g.append(1.0 / ((1 - P.nu ** 2) / P.E + (1 - pl.nu ** 2) / pl.E))
             mut_g.append(pl.mu_t)
             mur_g.append(pl.mu_r * float(self.r[ga[k]]))

@@ -86,3 +86,22 @@ def box_geoms(lo, hi, mu=0.3):
     for g in gs:
         g.mu_t, g.mu_r = mu, 0.01
     return gs
+
+
+def primitive_cloud(n=150, seed=7):
+    """A compressed cloud in a frictional box, pressed by an oblique box
+    (translating down and sideways) and a tilted cylinder (translating): the
+    contacts include box faces, edges and corners, and cylinder caps, sides
+    and rims.  Primitives 5 (box) and 6 (cylinder) follow the five walls."""
+    from scipy.spatial.transform import Rotation
+    x, r = compressed_cloud(n, seed=seed)
+    lo, hi = x.min(0) - 0.004, x.max(0) + 0.004
+    geoms = box_geoms(lo, hi)
+    c = (lo + hi) / 2
+    Rb = Rotation.from_euler("xyz", [0.3, -0.2, 0.5]).as_matrix().reshape(-1)
+    Rc = Rotation.from_euler("xyz", [0.6, 0.4, 0.0]).as_matrix().reshape(-1)
+    geoms.append(beds.GeomSpec(beds.BOX, (c[0], c[1], hi[2] - 0.004), tuple(Rb), (0.012, 0.008, 0.005),
+                               v=(0.01, 0.0, -0.05), mu_t=0.4, mu_r=0.02))
+    geoms.append(beds.GeomSpec(beds.CYLINDER, (lo[0] + 0.01, lo[1] + 0.01, c[2]), tuple(Rc),
+                               he=(0.007, 0.0, 0.006), v=(0.0, 0.02, 0.0), mu_t=0.4, mu_r=0.02))
+    return x, r, geoms

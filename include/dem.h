@@ -172,7 +172,10 @@ dem_status dem_create_batch(const dem_bed_desc* descs, int32_t nbeds, void* stre
 /* Autotuner: times trial_steps steps (after one untimed step) of every sweep
  * layout (lanes 0, 1, 2, 4, 8; the resident layout 16 is opt-in), keeps the
  * fastest, then times re-sort periods 5, 10, 20, 50 and keeps the fastest.
- * The bed advances by those steps: call it in place of warm-up steps.  Choices are returned through lanes_out and
+ * Last, it sizes the contact storage to 1.5 times the contacts the trial
+ * steps needed (plus 1024; larger or smaller than before), which later
+ * overflows grow as usual.  The bed advances by those steps: call it in place
+ * of warm-up steps.  Choices are returned through lanes_out and
  * resort_out (either may be NULL) and stay in effect.  Synchronises. */
 dem_status dem_autotune(dem_bed* bed, int32_t trial_steps, int32_t* lanes_out, int32_t* resort_out);
 
@@ -263,11 +266,17 @@ dem_status dem_set_plate_load(dem_bed* bed, int32_t geom, const double force[3])
  * that open or close inside the window are not differentiated.
  *
  * dem_record: advance the bed nsteps steps (as dem_step) and keep a checkpoint
- * of its state every ckpt_every steps.  forces (may be NULL): host or device
+ * of its state every ckpt_every steps (0: the interval that minimises the
+ * memory of checkpoints plus one segment's tapes, about
+ * sqrt(nsteps * checkpoint / tape of one step); the reverse pass recomputes
+ * each step once whatever the interval).  forces (may be NULL): host or device
  * buffer of nsteps * n_geom * 3 doubles, the force on each primitive in each
  * step [N], the same numbers dem_read_forces returns after that step.
- * Synchronises.  Requirements: every primitive is a plane that does not spin,
- * every bed of the object takes the same n_it; else DEM_ERR_ARG.  Memory:
+ * Synchronises.  Requirements: no primitive spins (planes, oriented boxes and
+ * cylinders that translate are differentiated, the normal's dependence on the
+ * contact's place on a box edge or corner, a cylinder side or rim included), no
+ * load-driven group, every bed of the object takes the same n_it, the Jacobi
+ * solver, no impact stage; else DEM_ERR_ARG.  Memory:
  * one checkpoint (positions, velocities, warm start: about 100 B per particle
  * and 40 B per contact) per ckpt_every steps.
  *

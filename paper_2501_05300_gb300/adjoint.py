@@ -5,7 +5,8 @@ theta = (k_n scale, mu_t, mu_r) and returns the force on every primitive in
 every step as a tensor that autograd differentiates with respect to theta:
 the backward pass is the library's hand-written adjoint of the step
 (dem_step_adjoint), along the contact set of every step, with the window
-recomputed from checkpoints taken every `ckpt_every` steps.
+recomputed from checkpoints taken every `ckpt_every` steps (0: the interval
+that minimises memory, chosen by the library).
 
 `deviatoric_stress` turns the wall forces of a box triaxial cell (Sec. 3.2)
 into sigma_1 - sigma_3 per step, so that, for instance,
@@ -43,7 +44,7 @@ class GeomForces(torch.autograd.Function):
         return torch.as_tensor(g, dtype=ctx.theta_dtype, device=ctx.theta_device), None, None, None
 
 
-def geom_forces(bed, theta, nsteps, ckpt_every=20):
+def geom_forces(bed, theta, nsteps, ckpt_every=0):
     """Forces on the bed's primitives over nsteps steps, differentiable in theta.
     The bed is left after the window; each call continues from where it is."""
     return GeomForces.apply(theta, bed, int(nsteps), int(ckpt_every))

@@ -88,6 +88,7 @@ struct TapeStep {
     float4* c_warm = nullptr;       // [2 nc] world-frame warm-start impulse
     // sphere-geometry contacts [ngc]
     float4* grec = nullptr;         // [6 ngc]
+    float* gdn = nullptr;           // [9 ngc] dn/dx of each contact's normal (world, row-major)
     float* gdelta = nullptr;
     int* g_prev = nullptr;
     float4* g_warm = nullptr;       // [2 ngc]
@@ -314,6 +315,81 @@ static __device__ __forceinline__ float rows_delta_bar(const SimParams& P, float
     return db;
 }
 
+// Derivative of a sphere-primitive contact's unit normal with respect to the
+// sphere centre, dn/dx (world frame, row-major), for the closest-point cases
+// of geom_hit.  With e = q - cl(q) the offset of the local centre q from its
+// clamped point cl and d = |e|, n_l = e / d, so dn_l/dq = (I - n_l n_l^T)
+// (I - dcl/dq) / d: zero on a face or cap (the clamped axis is n_l's),
+// (I - n n^T - t t^T) / d along a box edge of direction t, (I - n n^T) / d at a
+// corner, (I - u u^T) / rho in the plane normal to the axis on a cylinder's
+// side (u radial, rho the distance to the axis), and the general product at a
+// rim.  A centre inside the primitive takes the nearest face (zero) or, in a
+// cylinder's radial case, the radial direction (I - u u^T) / rho.  A plane's
+// normal is fixed.  dn/dx = R (dn_l/dq) R^T.
+static __device__ void geom_dn_dx(const GeomDev& g, double x0, double x1, double x2, float* out) {
+    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (g.type != DEM_GEOM_PLANE) {
+        const double d0 = x0 - g.c[0], d1 = x1 - g.c[1], d2 = x2 - g.c[2];
+        double q[3], cl[3], C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int j = 0; j < 3; ++j) q[j] = g.R[j] * d0 + g.R[3 + j] * d1 + g.R[6 + j] * d2;
+        bool inside_radial = false;
+        double rho = 0.0;
+        if (g.type == DEM_GEOM_BOX) {
+            for (int k = 0; k < 3; ++k) {
+                cl[k] = q[k] < -g.he[k] ? -g.he[k] : (q[k] > g.he[k] ? g.he[k] : q[k]);
+                C[k][k] = (q[k] < -g.he[k] || q[k] > g.he[k]) ? 0.0 : 1.0;
+            }
+        } else {
+            const double Rc = g.he[0], H = g.he[2];
+            const double rho2 = q[0] * q[0] + q[1] * q[1];
+            rho = sqrt(rho2);
+            if (rho2 > Rc * Rc) {
+                const double s = Rc / rho, ux = q[0] / rho, uy = q[1] / rho;
+                cl[0] = q[0] * s; cl[1] = q[1] * s;
+                C[0][0] = s * (1.0 - ux * ux); C[0][1] = -s * ux * uy;
+                C[1][0] = -s * ux * uy; C[1][1] = s * (1.0 - uy * uy);
+            } else {
+                cl[0] = q[0]; cl[1] = q[1];
+                C[0][0] = 1.0; C[1][1] = 1.0;
+            }
+            cl[2] = q[2] < -H ? -H : (q[2] > H ? H : q[2]);
+            C[2][2] = (q[2] < -H || q[2] > H) ? 0.0 : 1.0;
+            inside_radial = (H - fabs(q[2])) > (Rc - rho) && rho > 0.0;
+        }
+        const double e[3] = {q[0] - cl[0], q[1] - cl[1], q[2] - cl[2]};
+        const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+        double Ml[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        if (ee > 0.0) {
+            const double d = sqrt(ee);
+            const double nl[3] = {e[0] / d, e[1] / d, e[2] / d};
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        const double P = (i == k ? 1.0 : 0.0) - nl[i] * nl[k];
+                        const double Q = (k == j ? 1.0 : 0.0) - C[k][j];
+                        acc += P * Q;
+                    }
+                    Ml[i][j] = acc / d;
+                }
+        } else if (g.type == DEM_GEOM_CYLINDER && inside_radial) {
+            const double ux = q[0] / rho, uy = q[1] / rho;
+            Ml[0][0] = (1.0 - ux * ux) / rho; Ml[0][1] = -ux * uy / rho;
+            Ml[1][0] = -ux * uy / rho; Ml[1][1] = (1.0 - uy * uy) / rho;
+        }
+        // world: R Ml R^T (R row-major, column k = local axis k)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double acc = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) acc += g.R[3 * i + a] * Ml[a][b] * g.R[3 * j + b];
+                M[i][j] = acc;
+            }
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) out[3 * i + j] = (float)M[i][j];
+}
+
 // ---------------------------------------------------------------------------
 // tape kernels (forward recompute)
 // ---------------------------------------------------------------------------
@@ -354,6 +430,8 @@ __global__ void __launch_bounds__(AD_T) k_tape_bodies(SimParams P, DevBuf B, int
         T.g_prev[k] = src;
         T.g_warm[2 * (size_t)k] = src >= 0 ? B.glamW[q][2 * (size_t)src] : make_float4(0.f, 0.f, 0.f, 0.f);
         T.g_warm[2 * (size_t)k + 1] = src >= 0 ? B.glamW[q][2 * (size_t)src + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const double4_32a xi = B.pos[i];
+        geom_dn_dx(B.geom[g], xi.x, xi.y, xi.z, T.gdn + 9 * (size_t)k);
     }
 }
 
@@ -504,6 +582,16 @@ __global__ void __launch_bounds__(AD_T) k_adj_bodies(SimParams P, TapeStep T, Ad
             float3 linA, angA, angB;
             adj_update(R, P.eps_reg, l0, l1, f3(vi.v) - f3(r[3]), f3(vi.w), f3(r[4]), tva, twa, z, z, iIa, 0.f,
                        false, L0, L1, A0, A1, linA, angA, angB);
+            if (k == P.n_it - 1) {
+                // the step's force on the primitive, -(p_n n + p_t) / dt, depends on n
+                // through its normal part: n-bar += -p_n W / dt with the final p_n
+                const float wn = dot(R.n, f3(vi.v) - f3(r[3])) + R.sig * l0.x - R.rhs;
+                const float pn1 = fmaxf(0.0f, l0.x - R.invDn * wn);
+                const int g = __float_as_int(r[2].w);
+                const float s = -pn1 * P.inv_dt;
+                A0 = make_float4(A0.x + s * Q.wts[3 * g], A0.y + s * Q.wts[3 * g + 1], A0.z + s * Q.wts[3 * g + 2],
+                                 A0.w);
+            }
             Q.gL[2 * (size_t)kk] = L0;
             Q.gL[2 * (size_t)kk + 1] = L1;
             Q.gA[2 * (size_t)kk] = A0;
@@ -624,11 +712,21 @@ __global__ void __launch_bounds__(AD_T) k_adj_state(SimParams P, TapeStep T, Adj
                 float3 t1, t2;
                 tangent_basis(R.n, t1, t2);
                 const float3 pt = l0.y * t1 + l0.z * t2;
-                float3 nb = f3(A0);   // the normal of a plane is fixed: n-bar is not used
+                // n-bar: the sweeps' accumulations, then the body term, the warm
+                // start's projection and the velocity part of the right side
+                float3 nb = f3(A0);
                 float lab = A1.y, lbb = 0.f;
                 float Ln;
                 float3 Lt, Lr;
                 body_term(R, l0.x, pt, tva, twa, z, z, L0, L1, Ln, Lt, Lr, nb, lab, lbb);
+                if (P.n_it == 0) {   // the step's force is the warm start's: its normal part
+                    const int g = __float_as_int(T.grec[6 * (size_t)kk + 2].w);
+                    const float s = -l0.x * P.inv_dt;
+                    nb = nb + s * make_float3(Q.wts[3 * g], Q.wts[3 * g + 1], Q.wts[3 * g + 2]);
+                }
+                const float4 w0 = T.g_warm[2 * (size_t)kk];
+                const float3 ptw = make_float3(w0.y, w0.z, w0.w);
+                nb = nb - dot(Lt, R.n) * ptw - dot(ptw, R.n) * Lt;
                 const int pv = T.g_prev[kk];
                 if (pv >= 0) {
                     const float3 Lp = Lt - dot(Lt, R.n) * R.n;
@@ -636,8 +734,15 @@ __global__ void __launch_bounds__(AD_T) k_adj_state(SimParams P, TapeStep T, Adj
                     Q.glw_out[2 * (size_t)pv + 1] = make_float4(Lr.x, Lr.y, Lr.z, 0.f);
                 }
                 const float db = rows_delta_bar(P, T.gdelta[kk], R.sig, A0.w, A1.x, lab, 0.f);
-                // plane: delta = r - n.(x - c)
-                xb = xb - db * R.n;
+                const float3 vg = f3(T.grec[6 * (size_t)kk + 3]);   // the primitive's point velocity
+                nb = nb + (A1.x * P.ups) * (f3(s.v) - vg);
+                // delta = r - |x - q(x)|: d delta / dx = -n (the closest point is a
+                // minimiser); n(x) through dn/dx of the contact's case (zero for
+                // planes and faces)
+                const float* M = T.gdn + 9 * (size_t)kk;
+                xb = xb - db * R.n +
+                     make_float3(M[0] * nb.x + M[3] * nb.y + M[6] * nb.z, M[1] * nb.x + M[4] * nb.y + M[7] * nb.z,
+                                 M[2] * nb.x + M[5] * nb.y + M[8] * nb.z);
                 vbar = vbar + (A1.x * P.ups) * R.n;
                 gk += (double)A0.w * (double)(-R.sig / P.kn_scale);
             }
@@ -862,6 +967,7 @@ static dem_status tape_step(dem_bed* b, TapeStep& T, int nc, int ngc, int ncp, i
         c.take(T.c_self, nc); c.take(T.c_other, nc); c.take(T.c_pos, nc); c.take(T.rec, 3 * (size_t)nc);
         c.take(T.delta, nc); c.take(T.c_prev, nc); c.take(T.c_warm, 2 * (size_t)nc);
         c.take(T.grec, 6 * (size_t)ngc); c.take(T.gdelta, ngc); c.take(T.g_prev, ngc); c.take(T.g_warm, 2 * (size_t)ngc);
+        c.take(T.gdn, 9 * (size_t)ngc);
         c.take(T.lamA, it * nc); c.take(T.lamB, it * nc); c.take(T.glamA, it * ngc); c.take(T.glamB, it * ngc);
         c.take(T.v, it * n);
     });
@@ -951,10 +1057,8 @@ static dem_status check_supported(dem_bed* b) {
     for (int g = 0; g < P.ng; ++g) {
         if (hg[g].grp >= 0)
             return dem_fail(DEM_ERR_ARG, "the adjoint does not support load-driven primitives (primitive %d)", g);
-        if (hg[g].type != DEM_GEOM_PLANE)
-            return dem_fail(DEM_ERR_ARG, "the adjoint supports plane primitives only (primitive %d)", g);
         if (hg[g].w[0] != 0.0 || hg[g].w[1] != 0.0 || hg[g].w[2] != 0.0)
-            return dem_fail(DEM_ERR_ARG, "the adjoint supports planes that do not spin (primitive %d)", g);
+            return dem_fail(DEM_ERR_ARG, "the adjoint supports primitives that do not spin (primitive %d)", g);
     }
     return DEM_OK;
 }
@@ -1026,14 +1130,30 @@ extern "C" dem_status dem_checkpoint_free(dem_bed* b, dem_checkpoint* c) {
     return DEM_OK;
 }
 
+// Checkpoint interval that minimises the window's memory.  Every step is
+// recomputed exactly once in the reverse pass whatever the interval, so the
+// interval only trades checkpoints (nsteps / k of them) against the tapes of
+// one segment (k steps): k = sqrt(nsteps * checkpoint / tape of one step),
+// sizes estimated from the last step's contact count.
+static int auto_interval(dem_bed* b, int nsteps) {
+    int nc = 0, ngc = 0;
+    if (b->steps > 0) read_counts(b, (int)((b->steps - 1) & 1), &nc, &ngc);
+    const double n = std::max(b->P.n, 1), c = (double)nc + ngc;
+    const double ckpt = 100.0 * n + 40.0 * c;
+    const double tape = std::max(b->P.n_it, 1) * (24.0 * c + 32.0 * n) + 100.0 * c + 80.0 * n;
+    const int k = (int)std::lround(std::sqrt((double)nsteps * ckpt / tape));
+    return std::min(std::max(k, 1), nsteps);
+}
+
 extern "C" dem_status dem_record(dem_bed* b, int32_t nsteps, int32_t ckpt_every, double* forces) {
     dem_set_error_message("");
     if (!b) return dem_fail(DEM_ERR_ARG, "bed is NULL");
-    if (nsteps < 1 || ckpt_every < 1) return dem_fail(DEM_ERR_ARG, "nsteps and ckpt_every must be >= 1");
+    if (nsteps < 1 || ckpt_every < 0) return dem_fail(DEM_ERR_ARG, "need nsteps >= 1 and ckpt_every >= 0");
     if (b->faulted) return dem_fail(DEM_ERR_STATE, "the bed holds a latched device fault");
     DEM_CK(cudaSetDevice(b->dev));
     dem_status st = check_supported(b);
     if (st != DEM_OK) return st;
+    if (ckpt_every == 0) ckpt_every = auto_interval(b, nsteps);
     if ((st = ensure_state(b)) != DEM_OK) return st;
     AdjointState* S = b->adj;
     S->recorded = false;

@@ -958,22 +958,25 @@ static void drop_capacity_buffers(dem_bed* b) {
 }
 
 // New capacities: C sphere-sphere and G sphere-geometry contacts, own / geob
-// per body.  The warm-start lists of both parities (keys, world-frame impulses,
-// overlaps) are carried over; every other contact array is rebuilt by the next step.
+// per body (larger or smaller; a smaller one must still hold the contacts of
+// the last two steps).  The warm-start lists of both parities (keys,
+// world-frame impulses, overlaps) are carried over; every other contact array
+// is rebuilt by the next step.
 static dem_status grow_capacity(dem_bed* b, int64_t C, int64_t G, int own, int geob) {
     SimParams& P = b->P;
     DevBuf& B = b->B;
-    const size_t N = std::max(P.n, 1), C0 = P.max_contacts, G0 = P.max_geo;
+    const size_t N = std::max(P.n, 1);
+    const size_t C0 = std::min<size_t>(P.max_contacts, (size_t)C), G0 = std::min<size_t>(P.max_geo, (size_t)G);
     dem_status st = DEM_OK;
 #define RE(ptr, cnt, keep) \
     if (st == DEM_OK) st = regrow(b, (void**)&(ptr), (size_t)(cnt) * sizeof(*(ptr)), (size_t)(keep) * sizeof(*(ptr)))
-    if ((size_t)C != C0) {
+    if (C != P.max_contacts) {
         RE(B.c_other, C, 0); RE(B.c_key[0], C, C0); RE(B.c_key[1], C, C0); RE(B.rec, 3 * C, 0);
         RE(B.c_delta, C, C0); RE(B.lamA[0], C, 0); RE(B.lamA[1], C, 0); RE(B.lamB[0], C, 0); RE(B.lamB[1], C, 0);
         RE(B.lamW[0], 2 * C, 2 * C0); RE(B.lamW[1], 2 * C, 2 * C0); RE(B.inc, 2 * C, 0); RE(B.c_self, C, 0);
         RE(B.c_pos, C, 0); RE(B.c_idx, C, 0); RE(B.imp, 2 * C, 0);
     }
-    if ((size_t)G != G0) {
+    if (G != P.max_geo) {
         RE(B.g_key[0], G, G0); RE(B.g_key[1], G, G0); RE(B.grec, 6 * G, 0); RE(B.g_delta, G, G0);
         RE(B.glamA[0], G, 0); RE(B.glamA[1], G, 0); RE(B.glamB[0], G, 0); RE(B.glamB[1], G, 0);
         RE(B.glamW[0], 2 * G, 2 * G0); RE(B.glamW[1], 2 * G, 2 * G0); RE(B.g_body, G, 0); RE(B.gsh, G, 0);
@@ -1494,6 +1497,21 @@ extern "C" dem_status dem_autotune(dem_bed* b, int32_t trial_steps, int32_t* lan
         if (ms / n < best) { best = ms / n; best_resort = resort_opts[k]; }
     }
     b->resort_every = best_resort;
+    // contact storage: 1.5 x the contacts the trial steps needed (the arrays
+    // grow again by themselves if the bed later needs more)
+    if (b->P.n > 0 && !b->no_grow) {
+        int nc[2] = {0, 0}, ng[2] = {0, 0};
+        for (int q = 0; q < 2; ++q) {
+            CK(cudaMemcpyAsync(&nc[q], b->B.own_start[q] + b->P.n, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+            CK(cudaMemcpyAsync(&ng[q], b->B.geo_start[q] + b->P.n, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        }
+        CK(cudaStreamSynchronize(b->stream));
+        const int64_t mc = std::max(nc[0], nc[1]), mg = std::max(ng[0], ng[1]);
+        const int64_t C = std::min<int64_t>(mc + mc / 2 + 1024, 0x3fffffff);
+        const int64_t G = std::min<int64_t>(mg + mg / 2 + 1024, 0x3fffffff);
+        if (C != b->P.max_contacts || G != b->P.max_geo)
+            if ((st = grow_capacity(b, C, G, b->P.max_own, b->P.max_geo_body)) != DEM_OK) return st;
+    }
     if (lanes_out) *lanes_out = best_lanes;
     if (resort_out) *resort_out = best_resort;
     return DEM_OK;

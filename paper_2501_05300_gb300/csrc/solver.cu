@@ -436,6 +436,23 @@ int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s
 #ifndef DEM_BP_MINB
 #define DEM_BP_MINB 6
 #endif
+// Sphere-primitive contacts of objects without load-driven groups are updated
+// in the contact pass, which writes each one's impulse share (gsh); the body
+// pass then only adds shares (summed in the same order, so the results are
+// bit-identical).  Measured on the refined bed, its best shape is a
+// grid-stride over one resident wave of 6 blocks per SM at 80 registers,
+// each thread fetching the next body's range ahead (20.4 against 22.3 us per
+// sweep with the primitive contacts in the body pass).  With groups, the body
+// pass updates them itself after k_group_contacts.
+#ifndef DEM_GEO_IN_CP
+#define DEM_GEO_IN_CP 1
+#endif
+#ifndef DEM_BP_MINB_SHARES
+#define DEM_BP_MINB_SHARES 6
+#endif
+#ifndef DEM_BP_BLOCKS_PER_SM_SHARES
+#define DEM_BP_BLOCKS_PER_SM_SHARES 6   // 0: one body per thread
+#endif
 __global__ void __launch_bounds__(SV_T, DEM_CP_MINB) k_contact_pass(SimParams P, DevBuf B, int p, int it, int nact) {
     const int bad = *B.err;
     // contacts are stored in owner order: those of the active prefix come first
@@ -522,6 +539,38 @@ __global__ void __launch_bounds__(SV_T, DEM_CP_MINB) k_contact_pass(SimParams P,
         }
 #endif
     }
+#if DEM_GEO_IN_CP
+    if (P.n_groups == 0) {
+        // sphere-primitive contacts: the update geom_update makes, its impulse
+        // share on the body stored for the body pass
+        const int ngc = min(B.geo_start[p][nact], P.max_geo);
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ngc; k += stride) {
+            const int i = B.g_body[k];
+            const int nit = body_nit(P, B, i);
+            if (it >= nit) continue;
+            const float4* r = B.grec + 6 * (size_t)k;
+            const float4 g0 = r[0], g1 = r[1], g2 = r[2], g3 = r[3], g4 = r[4];
+            const float4 l0 = __ldcs(&B.glamA[src][k]);
+            const float2 l1 = __ldcs(&B.glamB[src][k]);
+            const VW me = vin[i];
+            const Upd u = contact_update(g0, g1, g2.x, 0.0f, g2.y, g2.z, l0, l1, f3(me.v) - f3(g3), f3(me.w),
+                                         f3(g4), P.eps_reg);
+            const float3 n = f3(g0);
+            if (it == nit - 1) {
+                write_world(B.glamW[p], k, n, u);
+            } else {
+                B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
+                B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
+            }
+            float3 La = make_float3(0.f, 0.f, 0.f), Aa = La;
+            add_impulse(n, u.t1, u.t2, g2.x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
+            Imp q;
+            q.a = make_float4(La.x, La.y, La.z, Aa.x);
+            q.b = make_float4(Aa.y, Aa.z, 0.f, 0.f);
+            B.gsh[k] = q;
+        }
+    }
+#endif
 }
 
 // A body's sphere-geometry contacts at sweep it: updated from its iterate,
@@ -563,6 +612,7 @@ void body_geom_contacts(const SimParams& P, const DevBuf& B, int p, int it, int 
 #endif
 // One body's sum of its impulse shares in incidence order, its geometry
 // contacts, and v = v* + M^-1 sum.
+template <bool GEO>
 static __device__ __forceinline__ void body_update(const SimParams& P, const DevBuf& B, int p, int it, int i,
                                                    int nit, int e0, int e1, int k0, int k1, float4 v0, float4 w0) {
     const bool last = it == nit - 1;
@@ -585,7 +635,16 @@ static __device__ __forceinline__ void body_update(const SimParams& P, const Dev
                 accA = accA + make_float3(qa[u].w, qb[u].x, qb[u].y);
             }
     }
-    if (k0 < k1) body_geom_contacts(P, B, p, it, i, k0, k1, last, accL, accA);
+    if (GEO) {
+        if (k0 < k1) body_geom_contacts(P, B, p, it, i, k0, k1, last, accL, accA);
+    } else {
+        for (int k = k0; k < k1; ++k) {   // shares of the contact pass, in list order
+            const float4 qa = __ldcs(&B.gsh[k].a);
+            const float2 qb = __ldcs(reinterpret_cast<const float2*>(&B.gsh[k].b));
+            accL = accL + f3(qa);
+            accA = accA + make_float3(qa.w, qb.x, qb.y);
+        }
+    }
     const float gm = v0.w > 0.0f ? P.dt : 0.0f;
     const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
     const float3 v = vs + v0.w * accL;
@@ -596,7 +655,11 @@ static __device__ __forceinline__ void body_update(const SimParams& P, const Dev
     B.vw[dst][i] = out;
 }
 
-__global__ void __launch_bounds__(SV_T, DEM_BP_MINB) k_body_pass(SimParams P, DevBuf B, int p, int it, int nact) {
+// GEO: the body updates its sphere-primitive contacts itself (objects with
+// load-driven groups); else it adds their shares from the contact pass
+template <bool GEO>
+__global__ void __launch_bounds__(SV_T, GEO ? DEM_BP_MINB : DEM_BP_MINB_SHARES)
+    k_body_pass(SimParams P, DevBuf B, int p, int it, int nact) {
     const int bad = *B.err;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     // the (first) body's incidence range and start velocity, before the wait
@@ -614,11 +677,11 @@ __global__ void __launch_bounds__(SV_T, DEM_BP_MINB) k_body_pass(SimParams P, De
     pdl_wait();
     pdl_trigger();
     if (bad) return;
-#if DEM_BP_BLOCKS_PER_SM > 0
+    if constexpr ((GEO ? DEM_BP_BLOCKS_PER_SM : DEM_BP_BLOCKS_PER_SM_SHARES) > 0) {
     // grid-stride over the bodies, the next body's range fetched ahead
     const int stride = gridDim.x * blockDim.x;
     for (; i < nact; i += stride) {
-        if (it < nit) body_update(P, B, p, it, i, nit, e0, e1, k0, k1, v0, w0);
+        if (it < nit) body_update<GEO>(P, B, p, it, i, nit, e0, e1, k0, k1, v0, w0);
         const int j = i + stride;
         if (j < nact) {
             nit = body_nit(P, B, j);
@@ -630,10 +693,10 @@ __global__ void __launch_bounds__(SV_T, DEM_BP_MINB) k_body_pass(SimParams P, De
             w0 = B.vw0[j].w;
         }
     }
-#else
+    } else {
     // one body per thread (else this bed has finished its sweeps)
-    if (i < nact && it < nit) body_update(P, B, p, it, i, nit, e0, e1, k0, k1, v0, w0);
-#endif
+    if (i < nact && it < nit) body_update<GEO>(P, B, p, it, i, nit, e0, e1, k0, k1, v0, w0);
+    }
 }
 
 // Contacts of load-driven groups at sweep it, one thread each: from the body's
@@ -901,12 +964,14 @@ int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int n
     }
     // two-pass sweep: contacts (grid-stride) then bodies
     const int cblocks = std::max(1, std::min(nblk(nact * 8, SV_T), DEM_CP_BLOCKS_PER_SM * sm_count()));
-    // bodies: one per thread, or grid-stride over DEM_BP_BLOCKS_PER_SM blocks per SM
-    const int bblocks = DEM_BP_BLOCKS_PER_SM > 0 ? std::max(1, std::min(nblk(nact, SV_T), DEM_BP_BLOCKS_PER_SM * sm_count()))
-                                                 : nblk(nact, SV_T);
+    // bodies: one per thread, or grid-stride over a fixed number of blocks per SM
+    const bool shares = DEM_GEO_IN_CP && P.n_groups == 0;
+    const int bps = shares ? DEM_BP_BLOCKS_PER_SM_SHARES : DEM_BP_BLOCKS_PER_SM;
+    const int bblocks = bps > 0 ? std::max(1, std::min(nblk(nact, SV_T), bps * sm_count())) : nblk(nact, SV_T);
     launch_pdl(k_contact_pass, cblocks, s, P, B, parity, it, nact);
     const int kg = launch_group_contacts(P, B, parity, it, s);
-    launch_pdl(k_body_pass, bblocks, s, P, B, parity, it, nact);
+    if (shares) launch_pdl(k_body_pass<false>, bblocks, s, P, B, parity, it, nact);
+    else launch_pdl(k_body_pass<true>, bblocks, s, P, B, parity, it, nact);
     return 2 + kg;
 }
 

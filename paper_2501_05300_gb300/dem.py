@@ -379,7 +379,7 @@ class Bed:
             return
         self.set_params(**p, lanes=-1)
 
-    def record(self, nsteps, ckpt_every=20):
+    def record(self, nsteps, ckpt_every=0):
         """Advance nsteps steps keeping checkpoints for the adjoint
         (dem_record).  Returns the force on every primitive in every step,
         shape (nsteps, n_geom, 3) [N]."""

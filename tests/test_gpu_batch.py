@@ -68,10 +68,14 @@ def test_autotune_picks_a_valid_configuration():
     x, r = compressed_cloud(5000, seed=41)
     lo, hi = x.min(0) - 0.004, x.max(0) + 0.004
     b = Bed(x, r, geoms=box_geoms(lo, hi), **params(n_it=30))
+    cap0 = b.info().contact_capacity
     lanes, resort = b.autotune(3)
     assert lanes in (0, 1, 2, 4, 8) and resort in (5, 10, 20, 50)
     info = b.info()
     assert info.lanes == lanes and info.resort_every == resort
+    # contact storage sized from the measured contacts (here smaller than 8 n)
+    assert info.contacts <= info.contact_capacity <= 1.5 * info.contacts + 1024 + 0.5 * info.contacts
+    assert info.contact_capacity < cap0
     b.step(3)
     b.sync()
     b.close()

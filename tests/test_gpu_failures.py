@@ -57,17 +57,17 @@ def test_total_capacity_overflow_grows_and_replays():
 
 def test_overflow_mid_run_after_resorts_matches_oracle():
     """A lattice falling into an open box: its sphere-sphere contacts pass a
-    capacity of 20 around step 220, after many re-sorts (the warm starts of
-    the last committed step carry over into the re-run).  The run equals one
-    with enough capacity bit for bit and tracks the oracle over 400 steps."""
+    capacity of 5 around step 180, after many re-sorts (the warm starts of the
+    last committed step carry over into the re-run).  The run equals one with
+    enough capacity bit for bit and tracks the oracle over 200 steps."""
     b = beds.settling_box(1000)
     p = params(n_it=100, dt=1e-4)
-    small = make_gpu(b.x, b.r, p, b.geoms, contact_capacity=20, resort_every=7)
+    small = make_gpu(b.x, b.r, p, b.geoms, contact_capacity=5, resort_every=7)
     big = make_gpu(b.x, b.r, p, b.geoms, resort_every=7)
     o = make_oracle(b.x, b.r, p, b.geoms)
     cap0 = small.info().contact_capacity
     grew_at = None
-    for k in range(40):
+    for k in range(20):
         small.step(10)
         big.step(10)
         o.step(10)

@@ -436,14 +436,14 @@ int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s
 #ifndef DEM_BP_MINB
 #define DEM_BP_MINB 6
 #endif
-// Sphere-primitive contacts of objects without load-driven groups are updated
-// in the contact pass, which writes each one's impulse share (gsh); the body
-// pass then only adds shares (summed in the same order, so the results are
-// bit-identical).  Measured on the refined bed, its best shape is a
-// grid-stride over one resident wave of 6 blocks per SM at 80 registers,
-// each thread fetching the next body's range ahead (20.4 against 22.3 us per
-// sweep with the primitive contacts in the body pass).  With groups, the body
-// pass updates them itself after k_group_contacts.
+// Sphere-primitive contacts are updated in the contact pass (those of a
+// load-driven group in k_group_contacts, between the passes), which writes
+// each one's impulse share (gsh); the body pass then only adds shares
+// (summed in the same order, so the results are bit-identical).  Measured on
+// the refined bed, its best shape is a grid-stride over one resident wave of
+// 6 blocks per SM at 80 registers, each thread fetching the next body's range
+// ahead (20.4 against 22.3 us per sweep with the primitive contacts in the
+// body pass).
 #ifndef DEM_GEO_IN_CP
 #define DEM_GEO_IN_CP 1
 #endif
@@ -540,15 +540,17 @@ __global__ void __launch_bounds__(SV_T, DEM_CP_MINB) k_contact_pass(SimParams P,
 #endif
     }
 #if DEM_GEO_IN_CP
-    if (P.n_groups == 0) {
+    {
         // sphere-primitive contacts: the update geom_update makes, its impulse
-        // share on the body stored for the body pass
+        // share on the body stored for the body pass (a load-driven group's
+        // contacts are left to k_group_contacts, which stores theirs)
         const int ngc = min(B.geo_start[p][nact], P.max_geo);
         for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ngc; k += stride) {
             const int i = B.g_body[k];
             const int nit = body_nit(P, B, i);
             if (it >= nit) continue;
             const float4* r = B.grec + 6 * (size_t)k;
+            if (P.n_groups > 0 && __float_as_int(r[5].w) >= 0) continue;
             const float4 g0 = r[0], g1 = r[1], g2 = r[2], g3 = r[3], g4 = r[4];
             const float4 l0 = __ldcs(&B.glamA[src][k]);
             const float2 l1 = __ldcs(&B.glamB[src][k]);
@@ -718,6 +720,15 @@ __global__ void __launch_bounds__(SV_T) k_group_contacts(SimParams P, DevBuf B, 
         B.glamA[dst][k] = make_float4(u.pn, u.pt1, u.pt2, u.pr.x);
         B.glamB[dst][k] = make_float2(u.pr.y, u.pr.z);
         if (it == nit - 1) write_world(B.glamW[p], k, f3(r[0]), u);
+#if DEM_GEO_IN_CP
+        // the impulse share on the body, for the shares-only body pass
+        float3 La = make_float3(0.f, 0.f, 0.f), Aa = La;
+        add_impulse(f3(r[0]), u.t1, u.t2, r[2].x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
+        Imp q;
+        q.a = make_float4(La.x, La.y, La.z, Aa.x);
+        q.b = make_float4(Aa.y, Aa.z, 0.f, 0.f);
+        B.gsh[k] = q;
+#endif
     }
 }
 
@@ -965,7 +976,7 @@ int launch_jacobi(const SimParams& P, const DevBuf& B, int parity, int it, int n
     // two-pass sweep: contacts (grid-stride) then bodies
     const int cblocks = std::max(1, std::min(nblk(nact * 8, SV_T), DEM_CP_BLOCKS_PER_SM * sm_count()));
     // bodies: one per thread, or grid-stride over a fixed number of blocks per SM
-    const bool shares = DEM_GEO_IN_CP && P.n_groups == 0;
+    const bool shares = DEM_GEO_IN_CP;
     const int bps = shares ? DEM_BP_BLOCKS_PER_SM_SHARES : DEM_BP_BLOCKS_PER_SM;
     const int bblocks = bps > 0 ? std::max(1, std::min(nblk(nact, SV_T), bps * sm_count())) : nblk(nact, SV_T);
     launch_pdl(k_contact_pass, cblocks, s, P, B, parity, it, nact);

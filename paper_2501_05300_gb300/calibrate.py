@@ -12,7 +12,8 @@ sigma_1 = K sigma_3, K = (1 + sin phi) / (1 - sin phi) (Mohr-Coulomb, no
 cohesion, as for the paper's dry sand).  One cell per confining stress is
 consolidated, then sheared with the candidate theta to the axial strain of
 its peak; the residual is the mean over a window there of
-(sigma_1 - K sigma_3) / sigma_3, with the walls held during the window.
+(sigma_1 - K sigma_3) / sigma_3, the side walls held and the platen still
+shearing during the window.
 Because every evaluation re-shears the cell with the candidate theta, the
 sample's fabric belongs to that theta, and the Gauss-Newton iteration stops
 where the re-sheared peak meets the target.  The gradient is the derivative
@@ -45,8 +46,8 @@ class FailureWindow:
     consolidated to sigma3 and saved in `consolidated` (a checkpoint).  For a
     candidate theta the cell is restored, given theta, sheared with servoed
     side walls to `strain` (triaxial.shear), and then `steps` steps are
-    recorded with the walls held; the residual is the window mean of
-    (sigma_1 - K sigma_3) / sigma3."""
+    recorded with the side walls held and the platen still moving; the
+    residual is the window mean of (sigma_1 - K sigma_3) / sigma3."""
 
     def __init__(self, bed, consolidated, sigma3, K, strain, steps, rate=0.5, ckpt_every=20, reshear=True):
         self.bed, self.start, self.sigma3, self.K = bed, consolidated, float(sigma3), float(K)
@@ -73,7 +74,7 @@ class FailureWindow:
         if grad:
             J.backward()
             g = th.grad.numpy().copy()
-        self.last = dict(sigma1=float(s1.mean()), sigma3=float(s3.mean()))
+        self.last = dict(sigma1=float(s1.detach().mean()), sigma3=float(s3.detach().mean()))
         return float(J.detach()), g
 
 
@@ -100,7 +101,7 @@ class MatchWindow:
         if grad:
             J.backward()
             g = th.grad.numpy().copy()
-        self.last = dict(sigma1=float(s1.mean()), sigma3=float(s3.mean()))
+        self.last = dict(sigma1=float(s1.detach().mean()), sigma3=float(s3.detach().mean()))
         return float(J.detach()), g
 
 

@@ -111,8 +111,10 @@ def shear(bed, sigma3, rate, strain, chunk=20, vmax=0.05):
     """Drained shearing: the platen moves down at `rate` (axial strain per
     second, of the current height) while the side walls servo to sigma3,
     until the axial strain reaches `strain`.  Returns the samples
-    (axial strain, sigma_1, sigma_3) taken every chunk; the walls are held
-    when it returns."""
+    (axial strain, sigma_1, sigma_3) taken every chunk.  When it returns the
+    side walls are held and the platen keeps moving, so the steps that follow
+    go on shearing the sample (a window to differentiate, in which no wall is
+    servoed)."""
     sig, L = wall_stress(bed)
     h0 = float(L[2])
     out = []
@@ -122,11 +124,11 @@ def shear(bed, sigma3, rate, strain, chunk=20, vmax=0.05):
         s3 = float(np.mean([sig[g] for g in SIDE_WALLS]))
         s1 = wall_stress(bed, (beds.PLATEN,))[0][beds.PLATEN]
         out.append((e, s1, s3))
+        bed.apply_plate_velocity(beds.PLATEN, (0.0, 0.0, -rate * float(L[2])))
         if e >= strain:
             break
-        bed.apply_plate_velocity(beds.PLATEN, (0.0, 0.0, -rate * float(L[2])))
         bed.step(chunk)
-    hold(bed)
+    hold(bed, SIDE_WALLS)
     return np.array(out)
 
 

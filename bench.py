@@ -545,6 +545,22 @@ def prepare_triaxial(dem, lanes=0, n=TRIAX_N, seed=2505, max_steps=8000, spec=No
     return bed, dict(consolidation_steps=steps, n_it=nit, height=h, stress=sig)
 
 
+def squeezed_triaxial(dem, lanes=0, n=TRIAX_N, nit=0):
+    """The triaxial cell with its lattice squeezed to contact instead of
+    consolidated (beds.triaxial_cell, squeeze 0.095: ~3 contacts per sphere,
+    as after consolidation), the platen moving at the shear rate, test
+    friction, dt 1e-5 s, N_it from Eq. 8 unless given.  The same sizes with no
+    settling run: the shape for ncu captures of the reverse pass."""
+    spec = beds.triaxial_cell(n, squeeze=0.095, v_top=-TRIAX_RATE * 0.2)
+    m = spec.material
+    h = float(spec.box[2])
+    nit = nit or rules.n_iterations(rules.network_length_uniform(h, 2 * 2.75e-3), 0.02)
+    bed = dem.Bed(spec.x, spec.r, geoms=spec.geoms, rho=m.rho, mu_t=m.mu_t, mu_r=m.mu_r, n_it=nit, dt=DT,
+                  gravity=(0.0, 0.0, 0.0), lanes=lanes)
+    bed.step(3)
+    return bed, dict(consolidation_steps=0, n_it=nit, height=h, stress=_wall_stress(bed)[0], squeezed=True)
+
+
 def oracle_gradient_sample(n=5000, squeeze=0.095, steps=1):
     """Time the FP64 gradient oracle (autograd through oracle/torch_step.py,
     as it stands) on a bounded sample of the triaxial workload: a 5,000-sphere
@@ -578,7 +594,10 @@ def run_triaxial(args):
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats()   # the peak of this measurement only
     t_prep = time.perf_counter()
-    bed, prep = prepare_triaxial(dem, lanes=max(args.lanes, 0))
+    if args.triax_squeezed:
+        bed, prep = squeezed_triaxial(dem, lanes=max(args.lanes, 0), nit=args.triax_nit)
+    else:
+        bed, prep = prepare_triaxial(dem, lanes=max(args.lanes, 0))
     if args.lanes < 0:
         bed.autotune(2)
     t_prep = time.perf_counter() - t_prep
@@ -1003,6 +1022,9 @@ def main():
     ap.add_argument("--triax-steps", type=int, default=TRIAX_STEPS, help="with --triaxial: window length")
     ap.add_argument("--triax-ckpt", type=int, default=TRIAX_CKPT, help="with --triaxial: checkpoint interval")
     ap.add_argument("--no-fd", action="store_true", help="with --triaxial: skip the finite differences")
+    ap.add_argument("--triax-squeezed", action="store_true",
+                    help="with --triaxial: the cell squeezed to contact, no consolidation run (for profiling)")
+    ap.add_argument("--triax-nit", type=int, default=0, help="with --triax-squeezed: N_it (0: Eq. 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-plain, adjoint/fwd and fine-bed side measurements of the default run")

@@ -75,7 +75,9 @@ typedef struct dem_geom {
 } dem_geom;
 
 /* Optional device allocator; when NULL the library uses cudaMallocAsync on the
- * bed's stream.  `stream` is the bed's cudaStream_t. */
+ * bed's stream.  `stream` is the bed's cudaStream_t.  It must return memory
+ * aligned to 256 bytes (as cudaMalloc and PyTorch's caching allocator do); a
+ * bed given anything else fails to create with DEM_ERR_CUDA. */
 typedef void* (*dem_alloc_fn)(size_t bytes, void* ctx, void* stream);
 typedef void (*dem_free_fn)(void* ptr, void* ctx, void* stream);
 

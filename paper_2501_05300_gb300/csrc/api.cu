@@ -67,6 +67,8 @@ static dem_status dalloc(dem_bed* b, void** p, size_t bytes) {
             return fail(DEM_ERR_CUDA, "cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
     }
     b->allocs.push_back(*p);
+    // kernels move 16- and 32-byte records with vector loads and stores
+    if ((uintptr_t)*p & 255) return fail(DEM_ERR_CUDA, "device allocation %p is not 256-byte aligned", *p);
     return DEM_OK;
 }
 

@@ -203,6 +203,61 @@ static __device__ __forceinline__ float sub_sum(float v) {
 static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 static __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// 32-byte records (a body's velocities VW, an impulse share Imp) move in one
+// 256-bit vector access (sm_100 and later) instead of two 128-bit ones: half
+// the load/store requests on the sweep's gathers.  Both types are 32-byte
+// aligned and every device array starts on a 256-byte boundary (checked at
+// allocation).  The loads are volatile so that they stay after
+// griddepcontrol.wait; the share loads stream (evict first).
+#ifndef DEM_V8
+#define DEM_V8 1
+#endif
+static __device__ __forceinline__ VW ld_vw(const VW* q) {
+#if DEM_V8
+    VW r;
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(r.v.x), "=f"(r.v.y), "=f"(r.v.z), "=f"(r.v.w), "=f"(r.w.x), "=f"(r.w.y), "=f"(r.w.z),
+                   "=f"(r.w.w)
+                 : "l"(q));
+    return r;
+#else
+    return *q;
+#endif
+}
+static __device__ __forceinline__ void st_vw(VW* q, const VW& r) {
+#if DEM_V8
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(q), "f"(r.v.x), "f"(r.v.y),
+                 "f"(r.v.z), "f"(r.v.w), "f"(r.w.x), "f"(r.w.y), "f"(r.w.z), "f"(r.w.w)
+                 : "memory");
+#else
+    *q = r;
+#endif
+}
+static __device__ __forceinline__ void share_store(Imp* q, float3 L, float3 A) {
+#if DEM_V8
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %7};" ::"l"(q), "f"(L.x), "f"(L.y),
+                 "f"(L.z), "f"(A.x), "f"(A.y), "f"(A.z), "f"(0.0f)
+                 : "memory");
+#else
+    Imp v;
+    v.a = make_float4(L.x, L.y, L.z, A.x);
+    v.b = make_float4(A.y, A.z, 0.f, 0.f);
+    *q = v;
+#endif
+}
+static __device__ __forceinline__ void share_load_cs(const Imp* q, float3& L, float3& A) {
+#if DEM_V8
+    asm volatile("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, _, _}, [%6];"
+                 : "=f"(L.x), "=f"(L.y), "=f"(L.z), "=f"(A.x), "=f"(A.y), "=f"(A.z)
+                 : "l"(q));
+#else
+    const float4 a = __ldcs(&q->a);
+    const float2 b = __ldcs(reinterpret_cast<const float2*>(&q->b));
+    L = f3(a);
+    A = make_float3(a.w, b.x, b.y);
+#endif
+}
+
 template <int T, bool UPDATE>
 __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, int it) {
     if (*B.err) return;
@@ -222,7 +277,7 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
     const float2* __restrict__ lBin = B.lamB[src];
     float3 accL = make_float3(0.f, 0.f, 0.f), accA = make_float3(0.f, 0.f, 0.f);
     if (active) {
-        const VW me = vin[i];
+        const VW me = ld_vw(vin + i);
         const float3 vi = f3(me.v), wi = f3(me.w);
         const int e1 = B.inc_start[i + 1];
         int e = B.inc_start[i] + lane;
@@ -240,7 +295,7 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
             if (UPDATE) {
                 const int j = ent.y;
                 const float4 r1 = B.rec[3 * (size_t)c + 1];
-                const VW other = vin[j];
+                const VW other = ld_vw(vin + j);
                 const float3 vj = f3(other.v), wj = f3(other.w);
                 const float3 dv = sideb ? vj - vi : vi - vj;
                 const float3 wa = sideb ? wj : wi, wb = sideb ? wi : wj;
@@ -287,7 +342,7 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
         accA = make_float3(sub_sum<T>(accA.x), sub_sum<T>(accA.y), sub_sum<T>(accA.z));
     }
     if (!active || lane != 0) return;
-    const VW s0 = B.vw0[i];
+    const VW s0 = ld_vw(B.vw0 + i);
     const float4 v0 = s0.v, w0 = s0.w;
     const float gm = v0.w > 0.0f ? P.dt : 0.0f;
     const float3 vs = make_float3(v0.x + gm * P.gx, v0.y + gm * P.gy, v0.z + gm * P.gz);
@@ -296,7 +351,7 @@ __global__ void __launch_bounds__(SV_T) k_sweep(SimParams P, DevBuf B, int p, in
     VW o;
     o.v = make_float4(v.x, v.y, v.z, v0.w);
     o.w = make_float4(w.x, w.y, w.z, w0.w);
-    B.vw[UPDATE ? dst : 0][i] = o;
+    st_vw(B.vw[UPDATE ? dst : 0] + i, o);
 }
 
 // ---------------------------------------------------------------------------
@@ -484,8 +539,8 @@ __global__ void __launch_bounds__(SV_T, DEM_CP_MINB) k_contact_pass(SimParams P,
             // the previous iterate is dead after this read: stream it (evict first)
             l0 = __ldcs(&B.lamA[src][c]);
             l1 = __ldcs(&B.lamB[src][c]);
-            A = vin[id.x];
-            Bv = vin[id.y];
+            A = ld_vw(vin + id.x);
+            Bv = ld_vw(vin + id.y);
         }
 #if DEM_CP_PIPE
         // the next contact's indices and rows, fetched while this one's
@@ -515,13 +570,8 @@ __global__ void __launch_bounds__(SV_T, DEM_CP_MINB) k_contact_pass(SimParams P,
             float3 La = make_float3(0.f, 0.f, 0.f), Aa = La, Lb = La, Ab = La;
             add_impulse(n, u.t1, u.t2, r2.x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
             add_impulse(n, u.t1, u.t2, r2.y, u.pn, u.pt1, u.pt2, u.pr, true, Lb, Ab);
-            Imp ia, ib;
-            ia.a = make_float4(La.x, La.y, La.z, Aa.x);
-            ia.b = make_float4(Aa.y, Aa.z, 0.f, 0.f);
-            ib.a = make_float4(Lb.x, Lb.y, Lb.z, Ab.x);
-            ib.b = make_float4(Ab.y, Ab.z, 0.f, 0.f);
-            B.imp[id.z] = ia;
-            B.imp[id.w] = ib;
+            share_store(&B.imp[id.z], La, Aa);
+            share_store(&B.imp[id.w], Lb, Ab);
         }
 #if DEM_CP_PIPE
         c = cn;
@@ -554,7 +604,7 @@ __global__ void __launch_bounds__(SV_T, DEM_CP_MINB) k_contact_pass(SimParams P,
             const float4 g0 = r[0], g1 = r[1], g2 = r[2], g3 = r[3], g4 = r[4];
             const float4 l0 = __ldcs(&B.glamA[src][k]);
             const float2 l1 = __ldcs(&B.glamB[src][k]);
-            const VW me = vin[i];
+            const VW me = ld_vw(vin + i);
             const Upd u = contact_update(g0, g1, g2.x, 0.0f, g2.y, g2.z, l0, l1, f3(me.v) - f3(g3), f3(me.w),
                                          f3(g4), P.eps_reg);
             const float3 n = f3(g0);
@@ -566,10 +616,7 @@ __global__ void __launch_bounds__(SV_T, DEM_CP_MINB) k_contact_pass(SimParams P,
             }
             float3 La = make_float3(0.f, 0.f, 0.f), Aa = La;
             add_impulse(n, u.t1, u.t2, g2.x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
-            Imp q;
-            q.a = make_float4(La.x, La.y, La.z, Aa.x);
-            q.b = make_float4(Aa.y, Aa.z, 0.f, 0.f);
-            B.gsh[k] = q;
+            share_store(&B.gsh[k], La, Aa);
         }
     }
 #endif
@@ -622,29 +669,25 @@ static __device__ __forceinline__ void body_update(const SimParams& P, const Dev
     float3 accL = make_float3(0.f, 0.f, 0.f), accA = accL;
     for (int e = e0; e < e1; e += DEM_BP_CHUNK) {
         // a share is read once, by its body: stream it
-        float4 qa[DEM_BP_CHUNK];
-        float2 qb[DEM_BP_CHUNK];
+        float3 qL[DEM_BP_CHUNK], qA[DEM_BP_CHUNK];
+#pragma unroll
+        for (int u = 0; u < DEM_BP_CHUNK; ++u)
+            if (e + u < e1) share_load_cs(&B.imp[e + u], qL[u], qA[u]);
 #pragma unroll
         for (int u = 0; u < DEM_BP_CHUNK; ++u)
             if (e + u < e1) {
-                qa[u] = __ldcs(&B.imp[e + u].a);
-                qb[u] = __ldcs(reinterpret_cast<const float2*>(&B.imp[e + u].b));
-            }
-#pragma unroll
-        for (int u = 0; u < DEM_BP_CHUNK; ++u)
-            if (e + u < e1) {
-                accL = accL + f3(qa[u]);
-                accA = accA + make_float3(qa[u].w, qb[u].x, qb[u].y);
+                accL = accL + qL[u];
+                accA = accA + qA[u];
             }
     }
     if (GEO) {
         if (k0 < k1) body_geom_contacts(P, B, p, it, i, k0, k1, last, accL, accA);
     } else {
         for (int k = k0; k < k1; ++k) {   // shares of the contact pass, in list order
-            const float4 qa = __ldcs(&B.gsh[k].a);
-            const float2 qb = __ldcs(reinterpret_cast<const float2*>(&B.gsh[k].b));
-            accL = accL + f3(qa);
-            accA = accA + make_float3(qa.w, qb.x, qb.y);
+            float3 qL, qA;
+            share_load_cs(&B.gsh[k], qL, qA);
+            accL = accL + qL;
+            accA = accA + qA;
         }
     }
     const float gm = v0.w > 0.0f ? P.dt : 0.0f;
@@ -654,7 +697,7 @@ static __device__ __forceinline__ void body_update(const SimParams& P, const Dev
     VW out;
     out.v = make_float4(v.x, v.y, v.z, v0.w);
     out.w = make_float4(w.x, w.y, w.z, w0.w);
-    B.vw[dst][i] = out;
+    st_vw(B.vw[dst] + i, out);
 }
 
 // GEO: the body updates its sphere-primitive contacts itself (objects with
@@ -673,8 +716,9 @@ __global__ void __launch_bounds__(SV_T, GEO ? DEM_BP_MINB : DEM_BP_MINB_SHARES)
         e1 = B.inc_start[i + 1];
         k0 = B.geo_start[p][i];
         k1 = B.geo_start[p][i + 1];
-        v0 = B.vw0[i].v;
-        w0 = B.vw0[i].w;
+        const VW s0 = ld_vw(B.vw0 + i);
+        v0 = s0.v;
+        w0 = s0.w;
     }
     pdl_wait();
     pdl_trigger();
@@ -691,8 +735,9 @@ __global__ void __launch_bounds__(SV_T, GEO ? DEM_BP_MINB : DEM_BP_MINB_SHARES)
             e1 = B.inc_start[j + 1];
             k0 = B.geo_start[p][j];
             k1 = B.geo_start[p][j + 1];
-            v0 = B.vw0[j].v;
-            w0 = B.vw0[j].w;
+            const VW s0 = ld_vw(B.vw0 + j);
+            v0 = s0.v;
+            w0 = s0.w;
         }
     }
     } else {
@@ -724,10 +769,7 @@ __global__ void __launch_bounds__(SV_T) k_group_contacts(SimParams P, DevBuf B, 
         // the impulse share on the body, for the shares-only body pass
         float3 La = make_float3(0.f, 0.f, 0.f), Aa = La;
         add_impulse(f3(r[0]), u.t1, u.t2, r[2].x, u.pn, u.pt1, u.pt2, u.pr, false, La, Aa);
-        Imp q;
-        q.a = make_float4(La.x, La.y, La.z, Aa.x);
-        q.b = make_float4(Aa.y, Aa.z, 0.f, 0.f);
-        B.gsh[k] = q;
+        share_store(&B.gsh[k], La, Aa);
 #endif
     }
 }

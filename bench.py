@@ -42,7 +42,7 @@ N_IT = rules.n_iterations(rules.network_length_refined(4.0, 5e-3, 40e-3, 2.0, 0.
 # DRAM bytes of one two-pass sweep of this workload (k_contact_pass + k_body_pass), from one ncu
 # capture of dram__bytes_read.sum + dram__bytes_write.sum with cold caches; stale (None) for any
 # other layout
-SWEEP_TRAFFIC_TWO_PASS = 53.32e6 + 1.39e6 + 41.80e6
+SWEEP_TRAFFIC_TWO_PASS = 53.32e6 + 1.40e6 + 41.80e6
 # algorithmic bytes of one Jacobi sweep (per contact: 48 B row data + 24 B
 # impulse read + 24 B written; per particle: v,w read, v*,w* read, v,w written)
 BYTES_PER_CONTACT = 96
@@ -500,6 +500,19 @@ TRIAX_CKPT = 0           # checkpoint interval of the adjoint window (0: chosen 
 TRIAX_WORKLOAD = ("triaxial cell: 50k spheres r~U[2.5,3.0] mm, consolidated to 100 kPa, axial strain rate "
                   "0.5/s, dt 1e-5 s; d(mean deviatoric stress over 400 steps)/d(k_n scale, mu_t, mu_r), "
                   "checkpoint interval chosen for least memory")
+
+
+def triax_workload(args):
+    """TRIAX_WORKLOAD, or what --triax-squeezed / --triax-steps / --triax-ckpt /
+    --triax-nit change in it."""
+    if not args.triax_squeezed and args.triax_steps == TRIAX_STEPS and args.triax_ckpt == TRIAX_CKPT:
+        return TRIAX_WORKLOAD
+    prep = ("squeezed to contact (no consolidation run)" if args.triax_squeezed else "consolidated to 100 kPa")
+    nit = f", N_it {args.triax_nit}" if args.triax_squeezed and args.triax_nit else ""
+    ck = "chosen for least memory" if args.triax_ckpt == 0 else str(args.triax_ckpt)
+    return (f"triaxial cell: 50k spheres r~U[2.5,3.0] mm, {prep}, platen at axial strain rate 0.5/s, dt 1e-5 s{nit}; "
+            f"d(mean deviatoric stress over {args.triax_steps} steps)/d(k_n scale, mu_t, mu_r), "
+            f"checkpoint interval {ck}")
 
 
 def _wall_stress(bed, walls=range(6)):
@@ -1113,7 +1126,7 @@ def main():
         print(json.dumps({"metric": "adjoint/fwd cost", "value": r["adjoint_over_forward"], "unit": "x",
                           "higher_is_better": False, "n_gpus": 1, "steps": args.triax_steps,
                           "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
-                          "config": {"workload": TRIAX_WORKLOAD, "ckpt_every": args.triax_ckpt,
+                          "config": {"workload": triax_workload(args), "ckpt_every": args.triax_ckpt,
                                      **{k: v for k, v in r.items() if k != "adjoint_over_forward"}}}))
         return
     if args.fine:

@@ -204,11 +204,13 @@ static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol
 static __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 // 32-byte records (a body's velocities VW, an impulse share Imp) move in one
-// 256-bit vector access (sm_100 and later) instead of two 128-bit ones: half
-// the load/store requests on the sweep's gathers.  Both types are 32-byte
-// aligned and every device array starts on a 256-byte boundary (checked at
-// allocation).  The loads are volatile so that they stay after
-// griddepcontrol.wait; the share loads stream (evict first).
+// 256-bit vector access (sm_100 and later).  For the body pass's share loads,
+// formerly a 128-bit and a 64-bit load, this halves the load requests and
+// the L1 throttling (measured on the refined bed: 20.3 -> 19.9 us per sweep);
+// elsewhere it fixes the access width.  Both types are 32-byte aligned and
+// every device array starts on a 256-byte boundary (checked at allocation).
+// The loads are volatile so that they stay after griddepcontrol.wait; the
+// share loads stream (evict first).
 #ifndef DEM_V8
 #define DEM_V8 1
 #endif

@@ -520,7 +520,7 @@ static dem_status create_impl(const dem_bed_desc* descs, int nbeds, void* stream
     AL(B.committed, 1); AL(B.need, 2);
     AL(B.lvl_lo, 3 * (size_t)L); AL(B.lvl_hi, 3 * (size_t)L); AL(B.tolv, 2);
     AL(B.body_cell, N); AL(B.cell_cnt, NC + 1); AL(B.cell_start, NC + 1); AL(B.cell_fill, NC + 1);
-    AL(B.cell_body, N); AL(B.cell_pos, N);
+    AL(B.cell_body, N); AL(B.cell_pos, N); AL(B.cell_id, N);
     AL(B.tmp_own, N * (size_t)P.max_own); AL(B.tmp_geo, N * (size_t)P.max_geo_body);
     AL(B.own_cnt, N + 1); AL(B.in_cnt, N + 1); AL(B.geo_cnt, N + 1); AL(B.in_fill, N + 1);
     AL(B.own_start[0], N + 1); AL(B.own_start[1], N + 1); AL(B.inc_start, N + 1);

@@ -124,8 +124,10 @@ __global__ void __launch_bounds__(BP_T) k_cell_fill(SimParams P, DevBuf B) {
     if (i >= P.n) return;
     int c = B.body_cell[i];
     int k = B.cell_start[c] + atomicAdd(&B.cell_fill[c], 1);
+    // candidates are read in cell order, without the hop through the slot
     B.cell_body[k] = i;
-    B.cell_pos[k] = B.posr[i];   // candidates are read in cell order, without the slot hop
+    B.cell_pos[k] = B.posr[i];
+    B.cell_id[k] = B.id[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -192,22 +194,20 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
 #pragma unroll
                 for (int r = 1; r < 9; ++r)
                     if (t >= pre[r]) k = st[r] + (t - pre[r]);
+                // the candidate's position, slot and id load together: a hit
+                // waits on one load, not on a chain through its slot
                 const float4 pj = B.cell_pos[k];
+                j = B.cell_body[k];
+                idj = B.cell_id[k];
                 const float R = pi.w + pj.w + tol;
                 const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
                 const float d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 < R * R) {
-                    j = B.cell_body[k];
-                    if (j != i) {
-                        idj = B.id[j];
-                        // same level: the lower id owns the pair
-                        if (!(l == li && idj < idi)) {
-                            // FP32 accept (see the header); only the band around
-                            // contact takes the FP64 test
-                            const float Rin = fmaxf(pi.w + pj.w - tol, 0.0f);
-                            hit = d2 < Rin * Rin || exact_pair(xi, B.pos[j]);
-                        }
-                    }
+                // not itself; same level: the lower id owns the pair
+                if (d2 < R * R && idj != idi && !(l == li && idj < idi)) {
+                    // FP32 accept (see the header); only the band around
+                    // contact takes the FP64 test
+                    const float Rin = fmaxf(pi.w + pj.w - tol, 0.0f);
+                    hit = d2 < Rin * Rin || exact_pair(xi, B.pos[j]);
                 }
             }
             const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & 0xffu;

@@ -142,6 +142,7 @@ struct DevBuf {
     int* cell_fill;     // [n_cells]
     int* cell_body;     // [n] slot of the particle in each cell position
     float4* cell_pos;   // [n] its FP32 centre and radius, in cell order
+    int* cell_id;       // [n] its stable id, in cell order
     // per-body candidate lists of the current step
     int2* tmp_own;      // [n * max_own] (other slot, other stable id)
     int* tmp_geo;       // [n * max_geo_body] primitive index

@@ -69,26 +69,25 @@ static __device__ __forceinline__ void warm_project(float4 w0, float4 w1, float3
 // ---------------------------------------------------------------------------
 // contact rows + warm start
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n || *B.err) return;
+// One thread per sphere-sphere contact (grid-stride): its rows from the two
+// bodies' state, and its warm start from the previous step's impulse of the
+// same pair, found among the contacts the owner held then.
+__global__ void __launch_bounds__(SV_T) k_setup_pairs(SimParams P, DevBuf B, int p) {
+    if (*B.err) return;
     const int q = p ^ 1;
-    const int prev = *B.resorted ? B.prev_of[i] : i;
-    const double4_32a xa = B.pos[i];
-    const float4 va = B.vw0[i].v, wa = B.vw0[i].w;
-    const int na = (B.inc_start[i + 1] - B.inc_start[i]) + (B.geo_start[p][i + 1] - B.geo_start[p][i]);
-    const float ra = (float)xa.w;
-
-    // sphere-sphere contacts owned by i (a = i)
-    const int os = B.own_start[p][i], oe = B.own_start[p][i + 1];
-    const int ps = B.own_start[q][prev], pe = B.own_start[q][prev + 1];
-    int kp = ps;
-    for (int c = os; c < oe; ++c) {
-        const int j = B.c_other[c];
+    const int nc = min(B.own_start[p][P.n], P.max_contacts);
+    const bool resorted = *B.resorted != 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const int i = B.c_self[c], j = B.c_other[c];
         const int key = B.c_key[p][c];
-        const double4_32a xb = B.pos[j];
+        const double4_32a xa = B.pos[i], xb = B.pos[j];
+        const float4 va = B.vw0[i].v, wa = B.vw0[i].w;
         const float4 vb = B.vw0[j].v, wb = B.vw0[j].w;
+        const int na = (B.inc_start[i + 1] - B.inc_start[i]) + (B.geo_start[p][i + 1] - B.geo_start[p][i]);
         const int nb = (B.inc_start[j + 1] - B.inc_start[j]) + (B.geo_start[p][j + 1] - B.geo_start[p][j]);
+        const int prev = resorted ? B.prev_of[i] : i;
+        const int ps = B.own_start[q][prev], pe = B.own_start[q][prev + 1];
+        const float ra = (float)xa.w;
         // distance in double, overlap via (R^2 - d^2) / (R + d) to avoid cancellation
         const double dx = __dsub_rn(xa.x, xb.x), dy = __dsub_rn(xa.y, xb.y), dz = __dsub_rn(xa.z, xb.z);
         const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
@@ -110,7 +109,9 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         B.rec[3 * (size_t)c + 1] = make_float4(rc.rhs, rc.sig, rc.invDt, rc.invDr);
         B.rec[3 * (size_t)c + 2] = make_float4(la, lb, P.mu_t, P.mu_r * dstar);
         B.c_delta[c] = delta;
-        // warm start from the previous step's impulse of the same pair
+        // warm start from the previous step's impulse of the same pair (each
+        // owner's list is sorted by key)
+        int kp = ps;
         while (kp < pe && B.c_key[q][kp] < key) ++kp;
         float4 l0 = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 l1 = make_float2(0.f, 0.f);
@@ -119,9 +120,21 @@ __global__ void __launch_bounds__(SV_T) k_setup(SimParams P, DevBuf B, int p) {
         B.lamA[0][c] = l0;
         B.lamB[0][c] = l1;
     }
+}
 
-    // sphere-geometry contacts
+// One thread per body: the rows and warm starts of its sphere-primitive contacts.
+__global__ void __launch_bounds__(SV_T) k_setup_geo(SimParams P, DevBuf B, int p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n || *B.err) return;
+    const int q = p ^ 1;
     const int gs = B.geo_start[p][i], ge = B.geo_start[p][i + 1];
+    if (gs >= ge) return;
+    const int prev = *B.resorted ? B.prev_of[i] : i;
+    const double4_32a xa = B.pos[i];
+    const float4 va = B.vw0[i].v, wa = B.vw0[i].w;
+    const int na = (B.inc_start[i + 1] - B.inc_start[i]) + (ge - gs);
+    const float ra = (float)xa.w;
+
     const int gps = B.geo_start[q][prev], gpe = B.geo_start[q][prev + 1];
     for (int k = gs; k < ge; ++k) {
         const int g = B.g_key[p][k];
@@ -447,9 +460,13 @@ __global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p
 
 static inline int nblk(int n, int t) { return n > 0 ? (n + t - 1) / t : 1; }
 
+static int sm_count();
+
 int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
-    k_setup<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity);
-    return 1;
+    const int cblocks = std::max(1, std::min(nblk(P.max_contacts, SV_T), 16 * sm_count()));
+    k_setup_pairs<<<cblocks, SV_T, 0, s>>>(P, B, parity);
+    k_setup_geo<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity);
+    return 2;
 }
 // ---------------------------------------------------------------------------
 // Two-pass sweep.  Contact pass: one thread per contact computes its update

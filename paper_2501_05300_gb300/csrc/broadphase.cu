@@ -136,13 +136,24 @@ __global__ void __launch_bounds__(BP_T) k_cell_fill(SimParams P, DevBuf B) {
 // PT threads per particle: the candidates of each row of cells are shared out
 // across the lanes, hits are compacted into the particle's list with a ballot
 // over the lanes, and lane 0 orders the list by the other particle's id.
+#ifndef PT
 #define PT 8
+#endif
+#define PT_MASK ((PT) == 32 ? 0xffffffffu : ((1u << (PT)) - 1u))
+// Candidates in the FP64 band are queued per particle and decided together
+// after the search, so that the FP64 predicate runs on full lanes once
+// instead of on one or two lanes in every round of candidates (GB300 issues
+// FP64 at 2 lanes per cycle per SM, whatever the number of active lanes).
+#ifndef DEM_PAIRS_DEFER
+#define DEM_PAIRS_DEFER 1
+#endif
+#define BAND_CAP 16
 __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gt / PT, lane = gt % PT;
     if (i >= P.n || *B.err) return;   // whole groups leave together
     const int grp = (threadIdx.x & 31) / PT;
-    const unsigned gmask = 0xffu << (grp * PT);
+    const unsigned gmask = PT_MASK << (grp * PT);
     const unsigned below = (1u << lane) - 1u;
     const float4 pi = B.posr[i];
     const double4_32a xi = B.pos[i];
@@ -152,6 +163,11 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
     int2* own = B.tmp_own + (size_t)i * P.max_own;
     int nown = 0;
     bool overflow = false;
+#if DEM_PAIRS_DEFER
+    __shared__ int2 band_q[BP_T / PT][BAND_CAP];
+    int2* bq = band_q[threadIdx.x / PT];
+    int nband = 0;
+#endif
     const int lend = B.lv[li].lend, gbeg = B.lv[li].g0, gend = B.lv[li].g1;
     for (int l = li; l < lend; ++l) {
         const LevelGrid g = B.lv[l];
@@ -187,7 +203,7 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
         // the rows' candidates as one list, shared out over the lanes in order
         for (int base = 0; base < pre[9]; base += PT) {
             const int t = base + lane;
-            bool hit = false;
+            bool hit = false, band = false;
             int j = 0, idj = 0;
             if (t < pre[9]) {
                 int k = st[0] + t;
@@ -207,10 +223,27 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
                     // FP32 accept (see the header); only the band around
                     // contact takes the FP64 test
                     const float Rin = fmaxf(pi.w + pj.w - tol, 0.0f);
+#if DEM_PAIRS_DEFER
+                    hit = d2 < Rin * Rin;
+                    band = !hit;
+#else
                     hit = d2 < Rin * Rin || exact_pair(xi, B.pos[j]);
+#endif
                 }
             }
-            const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & 0xffu;
+#if DEM_PAIRS_DEFER
+            {
+                // queue the band; a full queue decides the rest at once
+                const unsigned bb = (__ballot_sync(gmask, band) >> (grp * PT)) & PT_MASK;
+                if (band) {
+                    const int q = nband + __popc(bb & below);
+                    if (q < BAND_CAP) bq[q] = make_int2(j, idj);
+                    else hit = exact_pair(xi, B.pos[j]);
+                }
+                nband = min(nband + __popc(bb), BAND_CAP);
+            }
+#endif
+            const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & PT_MASK;
             if (hit) {
                 const int q = nown + __popc(bal & below);
                 if (q < P.max_own) {
@@ -223,6 +256,30 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
             nown += __popc(bal);
         }
     }
+#if DEM_PAIRS_DEFER
+    // the queued band, all lanes of the particle at once
+    __syncwarp(gmask);
+    for (int base = 0; base < nband; base += PT) {
+        const int t = base + lane;
+        bool hit = false;
+        int2 e = make_int2(0, 0);
+        if (t < nband) {
+            e = bq[t];
+            hit = exact_pair(xi, B.pos[e.x]);
+        }
+        const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & PT_MASK;
+        if (hit) {
+            const int q = nown + __popc(bal & below);
+            if (q < P.max_own) {
+                own[q] = e;
+                atomicAdd(&B.in_cnt[e.x], 1);
+            } else {
+                overflow = true;
+            }
+        }
+        nown += __popc(bal);
+    }
+#endif
     int ngeo = 0;
     int* gl = B.tmp_geo + (size_t)i * P.max_geo_body;
     for (int base = gbeg; base < gend; base += PT) {
@@ -232,7 +289,7 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
             const GeomDev& g = B.geom[gi];
             hit = geom_near(g, pi, tol_g) && geom_hit(g, xi.x, xi.y, xi.z, xi.w).hit;
         }
-        const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & 0xffu;
+        const unsigned bal = (__ballot_sync(gmask, hit) >> (grp * PT)) & PT_MASK;
         if (hit) {
             const int q = ngeo + __popc(bal & below);
             if (q < P.max_geo_body) gl[q] = gi;

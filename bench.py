@@ -42,7 +42,7 @@ N_IT = rules.n_iterations(rules.network_length_refined(4.0, 5e-3, 40e-3, 2.0, 0.
 # DRAM bytes of one two-pass sweep of this workload (k_contact_pass + k_body_pass), from one ncu
 # capture of dram__bytes_read.sum + dram__bytes_write.sum with cold caches; stale (None) for any
 # other layout
-SWEEP_TRAFFIC_TWO_PASS = 53.32e6 + 1.40e6 + 41.80e6
+SWEEP_TRAFFIC_TWO_PASS = 53.29e6 + 1.90e6 + 41.78e6
 # algorithmic bytes of one Jacobi sweep (per contact: 48 B row data + 24 B
 # impulse read + 24 B written; per particle: v,w read, v*,w* read, v,w written)
 BYTES_PER_CONTACT = 96

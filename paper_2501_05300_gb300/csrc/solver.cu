@@ -122,21 +122,20 @@ __global__ void __launch_bounds__(SV_T) k_setup_pairs(SimParams P, DevBuf B, int
     }
 }
 
-// One thread per body: the rows and warm starts of its sphere-primitive contacts.
+// One thread per sphere-primitive contact (grid-stride): its rows and warm start.
 __global__ void __launch_bounds__(SV_T) k_setup_geo(SimParams P, DevBuf B, int p) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n || *B.err) return;
+    if (*B.err) return;
     const int q = p ^ 1;
-    const int gs = B.geo_start[p][i], ge = B.geo_start[p][i + 1];
-    if (gs >= ge) return;
-    const int prev = *B.resorted ? B.prev_of[i] : i;
-    const double4_32a xa = B.pos[i];
-    const float4 va = B.vw0[i].v, wa = B.vw0[i].w;
-    const int na = (B.inc_start[i + 1] - B.inc_start[i]) + (ge - gs);
-    const float ra = (float)xa.w;
-
-    const int gps = B.geo_start[q][prev], gpe = B.geo_start[q][prev + 1];
-    for (int k = gs; k < ge; ++k) {
+    const int ngc = min(B.geo_start[p][P.n], P.max_geo);
+    const bool resorted = *B.resorted != 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ngc; k += gridDim.x * blockDim.x) {
+        const int i = B.g_body[k];
+        const int prev = resorted ? B.prev_of[i] : i;
+        const double4_32a xa = B.pos[i];
+        const float4 va = B.vw0[i].v, wa = B.vw0[i].w;
+        const int na = (B.inc_start[i + 1] - B.inc_start[i]) + (B.geo_start[p][i + 1] - B.geo_start[p][i]);
+        const float ra = (float)xa.w;
+        const int gps = B.geo_start[q][prev], gpe = B.geo_start[q][prev + 1];
         const int g = B.g_key[p][k];
         const GeomDev& G = B.geom[g];
         // closest point, recomputed with the same routine the detection used
@@ -465,7 +464,8 @@ static int sm_count();
 int launch_setup(const SimParams& P, const DevBuf& B, int parity, cudaStream_t s) {
     const int cblocks = std::max(1, std::min(nblk(P.max_contacts, SV_T), 16 * sm_count()));
     k_setup_pairs<<<cblocks, SV_T, 0, s>>>(P, B, parity);
-    k_setup_geo<<<nblk(P.n, SV_T), SV_T, 0, s>>>(P, B, parity);
+    const int gblocks = std::max(1, std::min(nblk(P.max_geo, SV_T), 4 * sm_count()));
+    k_setup_geo<<<gblocks, SV_T, 0, s>>>(P, B, parity);
     return 2;
 }
 // ---------------------------------------------------------------------------

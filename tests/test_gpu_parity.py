@@ -277,6 +277,45 @@ def far_pairs(m, seed, gap):
     return x, r
 
 
+def crowded_band(m, seed, gap):
+    """Sphere 0 at the origin and m spheres of the same size on the shell of
+    centre distance r_0 + r_k + g, g uniform in [-gap, gap]: every one of
+    them is a band pair of sphere 0 (which owns them, having the lowest id),
+    and they overlap one another deeply."""
+    rng = np.random.default_rng(seed)
+    r = np.full(m + 1, 5e-3, np.float32)
+    u = rng.normal(size=(m, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    d = 2 * float(r[0]) + rng.uniform(-gap, gap, m)
+    x = np.zeros((m + 1, 3))
+    x[1:] = u * d[:, None]
+    return x, r
+
+
+def test_contact_set_exact_with_more_band_pairs_than_one_queue():
+    """One sphere with 40 partners within a few nanometres of touching, more
+    than a particle's queue of band pairs holds (16): the pairs beyond it are
+    decided at once, the rest after the search, and the contact set equals
+    the exact predicate's (FP64 brute force)."""
+    x, r = crowded_band(40, 61, 2e-8)
+    p = params(n_it=4, gravity=(0.0, 0.0, 0.0))
+    g = make_gpu(x, r, p, ())
+    g.step(1)
+    a, b, _, _ = g.read_contacts()
+    got = set(zip(np.minimum(a, b).tolist(), np.maximum(a, b).tolist()))
+    ea, eb, _ = oracle.detect(x, r.astype(np.float64), np.arange(len(r), dtype=np.int32))
+    ref = set(zip(ea.tolist(), eb.tolist()))
+    assert got == ref
+    of0 = {q for pq in ref if 0 in pq for q in pq if q != 0}
+    assert 5 < len(of0) < 35      # both outcomes among sphere 0's band pairs
+    # the case has teeth: all 40 lie inside the FP32 band of sphere 0
+    absmax = np.abs(x).max()
+    tol = 4 * 2.0 ** -23 * (1.25 * absmax + 8 * 5e-3) + 8 * 2.0 ** -24 * 2 * 5e-3
+    dist = np.linalg.norm(x[1:], axis=1)
+    assert (np.abs(dist - 1e-2) < tol).sum() > 16
+    g.close()
+
+
 @pytest.mark.parametrize("vx", [6e6, -4e6])
 def test_contact_set_exact_far_from_origin(vx):
     """A bed created near the origin and thrown 40-60 m along x in one step

@@ -28,12 +28,22 @@ def contact_sets_equal(g, o):
     return ok, (a, b, lam, dl[order]), (oa, ob, olam, odl)
 
 
-def assert_impulses_close(lam, olam, tol):
+def assert_impulses_close(lam, olam, tol, floor=1e-2, per_contact=2e-4):
+    """Every component within tol of the largest impulse; the whole set within
+    tol in norm; and every contact that carries at least `floor` of the
+    largest impulse within `per_contact` of its own largest component (5x
+    tighter than the first bar implies for such a contact, tol / floor), so
+    that small contacts are held to their own size."""
     scale = np.abs(olam).max()
     assert scale > 0
     err = np.abs(lam - olam).max(axis=1) / scale
     assert err.max() < tol, (err.max(), np.argmax(err))
     assert np.linalg.norm(lam - olam) / np.linalg.norm(olam) < tol
+    own = np.abs(olam).max(axis=1)
+    big = own >= floor * scale
+    assert big.sum() > 0
+    rel = np.abs(lam - olam).max(axis=1)[big] / own[big]
+    assert rel.max() < per_contact, (rel.max(), np.quantile(rel, [0.5, 0.99]), int(big.sum()))
 
 
 def cloud_case(n, seed, n_it=60):

@@ -206,10 +206,10 @@ __global__ void __launch_bounds__(BP_T) k_pairs(SimParams P, DevBuf B) {
             bool hit = false, band = false;
             int j = 0, idj = 0;
             if (t < pre[9]) {
-                int k = st[0] + t;
+                int o = st[0];
 #pragma unroll
-                for (int r = 1; r < 9; ++r)
-                    if (t >= pre[r]) k = st[r] + (t - pre[r]);
+                for (int r = 1; r < 9; ++r) o = t >= pre[r] ? st[r] - pre[r] : o;
+                const int k = t + o;
                 // the candidate's position, slot and id load together: a hit
                 // waits on one load, not on a chain through its slot
                 const float4 pj = B.cell_pos[k];

@@ -396,7 +396,12 @@ __global__ void __launch_bounds__(SV_T) k_integrate(SimParams P, DevBuf B, int p
         x.z = __dadd_rn(x.z, __dmul_rn(h, (double)v.z));
         B.pos[i] = x;
         B.posr[i] = make_float4((float)x.x, (float)x.y, (float)x.z, (float)x.w);
-        for (int k = B.geo_start[p][i]; k < B.geo_start[p][i + 1]; ++k) {
+    }
+    if (ok) {
+        // the primitives' impulses, one thread per sphere-primitive contact (full
+        // lanes for the conversions to fixed point, which run on the FP64 pipe)
+        const int ngc = min(B.geo_start[p][P.n], P.max_geo);
+        for (int k = i; k < ngc; k += gridDim.x * blockDim.x) {
             const float4* r = B.grec + 6 * (size_t)k;
             const float4 r0 = r[0], r2 = r[2], r5 = r[5];
             const float4 W0 = B.glamW[p][2 * (size_t)k], W1 = B.glamW[p][2 * (size_t)k + 1];

@@ -463,6 +463,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     torch.cuda.synchronize()
+    batch.set_timing(True)
     e[0].record(stream)
     for _ in range(args.steps):
         batch.step(1)
@@ -475,6 +476,16 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_batch = e[0].elapsed_time(e[1]) / args.steps
     t_seq = e[2].elapsed_time(e[3]) / args.steps
+    _, jac_ms, ts = batch.read_timing()
+    batch.set_timing(False)
+    # the batch's sweeps against the HBM roofline: every bed's algorithmic bytes
+    # per sweep times its own N_it, over the sweeps' time per step
+    infos = [b.info() for b in single]
+    alg = sum(s["n_it"] * (BYTES_PER_CONTACT * (f.contacts + f.geom_contacts) + BYTES_PER_BODY * f.n)
+              for s, f in zip(specs, infos))
+    sweeps_ms = jac_ms / max(ts, 1)
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    achieved = alg / (sweeps_ms * 1e-3) / 1e9
     n = batch.n
     x0, v0, _ = batch.read_state()
     same = True
@@ -488,7 +499,10 @@ def run_batch(args):
                 particles=n, beds=len(specs), lanes=lanes, resort_every=resort,
                 batched_value=n / (t_batch * 1e-3), sequential_value=n / (t_seq * 1e-3),
                 n_it_range=[min(s["n_it"] for s in specs), max(s["n_it"] for s in specs)],
-                identical_to_sequential=same)
+                identical_to_sequential=same,
+                roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "sweeps_ms_per_step": sweeps_ms, "alg_bytes_per_step": alg,
+                          "kernel": "the Jacobi sweeps of all 36 beds (each bed's N_it)"})
 
 
 # differentiation workload: box triaxial cell (Sec. 3.2)

@@ -18,14 +18,17 @@
 // Execution, two layouts here (the resident one is in resident.cu), no atomics:
 // - two-pass (k_contact_pass + k_body_pass, chained by programmatic dependent
 //   launch): one thread per contact computes its update once and writes each
-//   body's impulse share; one thread per body sums its shares in incidence
-//   order and its geometry contacts;
+//   body's impulse share (the sphere-primitive contacts too; those of a
+//   load-driven group in k_group_contacts); a thread per body sums its shares
+//   in incidence order, then its primitive contacts' shares in list order;
 // - one kernel per sweep (k_sweep<T>): T threads per body walk its incidence
 //   list (ordered by the other body's stable id) and recompute each contact's
 //   update from the two bodies' previous iterates -- the same arithmetic on
 //   the same inputs at both ends, so both ends agree bit for bit -- write it
 //   if the body owns the contact, and add their own share of the impulse.
-// The contact update itself (sweep.cuh) is shared by every layout.
+// The contact update itself (sweep.cuh) is shared by every layout.  The rows
+// and warm starts are set up one thread per contact (k_setup_pairs,
+// k_setup_geo) before the sweeps.
 #include <algorithm>
 
 #include "dem_internal.cuh"
